@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the VeST coordinate-descent hot path on the Zipf workload.
+
+Workload (default): 3-order 100,000^3 tensor, 1e7 observed entries with
+Zipf(1.2) indices per mode, FP32 values from a planted sparse Tucker model,
+ranks (10, 10, 10), L_F lambda = 0.01; the fitted model starts U(0,1) dense.
+
+One step = one pass of the whole path: factor sweep over every mode,
+core sweep, loss, responsibility scores, prune.  This workload does not
+prune, so the prune runs its full selection with pr = 0 and changes nothing.
+value = (order * nnz) entry-mode updates per second of whole steps, all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank fits its own independent
+instance of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1904_02603_gb300 import datagen  # noqa: E402
+
+METRIC = "CD-sweep nnz-updates/s"
+UNIT = "entry-mode updates/s"
+FP32_LANES_PER_SM = 128
+GB300_SMS = 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="vest", choices=["vest", "reference"])
+    p.add_argument("--workload", default="c1", choices=sorted(datagen.WORKLOADS))
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
+    return p.parse_args()
+
+
+def workload_config(w: datagen.Workload, extra=None):
+    c = {"workload": w.name, "dims": list(w.dims), "ranks": list(w.ranks), "nnz": w.nnz, "index_dist": w.dist,
+         "zipf_s": w.zipf_s if w.dist == "zipf" else None, "reg": w.reg, "lambda": w.lam,
+         "core_density_planted": w.core_density, "factor_density_planted": w.factor_density, "noise": w.noise,
+         "init": "U(0,1) dense (Algorithm 2, line 1)", "data_seed": w.data_seed, "init_seed": w.init_seed}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def sample_problem(t: datagen.SparseTensor, n: int, seed: int = 0):
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(t.nnz, size=min(n, t.nnz), replace=False))
+    return t.idx[:, sel], t.val[sel].astype(np.float64)
+
+
+def oracle_step_time(t, st, n_sample: int, reg: int, lam: float):
+    """One full oracle iteration (factor sweep, core sweep, loss, responsibility, prune pr=0) on a sample."""
+    import oracle as O
+    idx, x = sample_problem(t, n_sample)
+    prob = O.Problem(t.dims, idx, x)
+    om = O.Model([f.astype(np.float64) for f in st.factors], st.core.astype(np.float64))
+    t0 = time.perf_counter()
+    O.sweep_factors(prob, om, reg, lam, -1)
+    O.sweep_core(prob, om, reg, lam)
+    O.loss(prob, om, reg, lam)
+    df, dc, _, _ = O.responsibility(prob, om)
+    O.prune(om, df, dc, 0.0)
+    return time.perf_counter() - t0, prob.nnz
+
+
+def oracle_rate(t, st, w, target_seconds: float):
+    reg = 0 if w.reg == "LF" else 1
+    probe_n = 4000
+    dt, n = oracle_step_time(t, st, probe_n, reg, w.lam)
+    n_target = int(min(t.nnz, max(probe_n, probe_n * target_seconds / max(dt, 1e-3))))
+    dt, n = oracle_step_time(t, st, n_target, reg, w.lam)
+    return len(t.dims) * n / dt, n, dt
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores, on bounded samples of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = datagen.WORKLOADS[args.workload]
+    t, st, _ = datagen.make(w)
+    reg = 0 if w.reg == "LF" else 1
+    per_step = min(10.0, 150.0 / max(args.steps + args.warmup, 1))
+    dt, n = oracle_step_time(t, st, 4000, reg, w.lam)
+    n_sample = int(min(t.nnz, max(4000, 4000 * per_step / max(dt, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_step_time(t, st, n_sample, reg, w.lam)
+    times = [oracle_step_time(t, st, n_sample, reg, w.lam)[0] for _ in range(args.steps)]
+    total = sum(times)
+    value = args.steps * len(t.dims) * n_sample / total
+    sample = (f"{n_sample} entries drawn uniformly from the workload's {t.nnz} (same dims, ranks, values, init); "
+              "one full iteration per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, {"sample_entries": n_sample, "parallelism": "single host thread"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index_for_smi(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_1904_02603_gb300 import vest as V
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1904_02603_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    V.load()
+
+    w = datagen.WORKLOADS[args.workload]
+    # every rank fits its own instance of the workload (weak scaling)
+    t, st, _ = datagen.make(w, data_seed=w.data_seed + rank, init_seed=w.init_seed + rank)
+    tdt = torch.float64 if w.dtype == "f64" else torch.float32
+    reg = V.REG_LF if w.reg == "LF" else V.REG_L1
+    ten = V.Tensor.from_host(t)
+    mdl = V.Model.from_host(st)
+    ix = V.vest_build_index(ten)
+    sc = V.make_scratch(ix, mdl)
+    stream = torch.cuda.current_stream()
+    N, nnz = len(t.dims), t.nnz
+    units_per_step = N * nnz
+
+    def step(model, index, evs=None):
+        if evs:
+            evs[0].record(stream)
+        V.vest_sweep_factors(index, model, reg, w.lam, -1, sc)
+        if evs:
+            evs[1].record(stream)
+        V.vest_sweep_core(index, model, reg, w.lam, sc)
+        if evs:
+            evs[2].record(stream)
+        loss = V.vest_loss(index, model, reg, w.lam, sc)
+        if evs:
+            evs[3].record(stream)
+        df, dc, _, _ = V.vest_responsibility(index, model, sc, with_resp=False)
+        if evs:
+            evs[4].record(stream)
+        V.vest_prune(model, df, dc, 0.0, sc)
+        if evs:
+            evs[5].record(stream)
+        return loss
+
+    for _ in range(args.warmup):
+        step(mdl, ix)
+    torch.cuda.synchronize()
+
+    ops = ["sweep_factors", "sweep_core", "loss", "responsibility", "prune"]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(gpu_index_for_smi(local))
+    time.sleep(0.5)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = V.vest_launch_count()
+    start.record(stream)
+    for k in range(args.steps):
+        loss = step(mdl, ix, evs[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    launches = V.vest_launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = start.elapsed_time(end)
+    op_ms = {op: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
+             for i, op in enumerate(ops)}
+    if world > 1:
+        tt = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    value = world * units_per_step * args.steps / (elapsed_ms / 1e3)
+    final_loss = loss.cpu().numpy().tolist()
+
+    # ---------------- end to end: host buffers in, loss out, through the public API
+    idx_h = torch.from_numpy(t.idx).pin_memory()
+    val_h = torch.from_numpy(t.val).pin_memory()
+    loss_h = torch.empty(5, dtype=torch.float64).pin_memory()
+    e2e_model = mdl.clone()
+    h2d = idx_h.numel() * idx_h.element_size() + val_h.numel() * val_h.element_size()
+    d2h = loss_h.numel() * loss_h.element_size()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        tdev = V.Tensor(t.dims, idx_h.to("cuda", non_blocking=True), val_h.to("cuda", non_blocking=True))
+        ixe = V.vest_build_index(tdev)
+        le = step(e2e_model, ixe)
+        loss_h.copy_(le, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_wall))
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = world * units_per_step * args.e2e_steps / (e2e_ms / 1e3)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---------------- roofline of the dominant kernel: the factor sweep
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = GB300_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    # algorithmic work per entry and mode (dense core): delta = |G| + |G|/J_n FMAs, row sums J_n + J_n(J_n+1)/2 FMAs
+    G = math.prod(w.ranks)
+    fma = sum(G + G // Jn + Jn + Jn * (Jn + 1) // 2 for Jn in w.ranks) / N
+    flops_sweep = 2.0 * fma * nnz * N
+    sweep_s = op_ms["sweep_factors"] / 1e3
+    achieved = flops_sweep / sweep_s / 1e12
+    # algorithmic bytes of one factor sweep (all modes): per mode nnz((N-1)*4 + s_val) + (I_n+1)*8 +
+    # 2 I_n J_n s_f + I_n J_n (mask) + sum_{k != n} I_k J_k s_f
+    s = 4 if w.dtype == "f32" else 8
+    bytes_sweep = 0
+    for n in range(N):
+        bytes_sweep += nnz * ((N - 1) * 4 + s) + (w.dims[n] + 1) * 8 + 2 * w.dims[n] * w.ranks[n] * s
+        bytes_sweep += w.dims[n] * w.ranks[n] + sum(w.dims[k] * w.ranks[k] * s for k in range(N) if k != n)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {"bound": "alu", "kernel": "vest_sweep_factors (all modes: task kernels + fix-up)",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "peak_source": f"FP32 FMA: {GB300_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz",
+                "traffic": None,
+                "algorithmic_flops_per_launch": flops_sweep, "algorithmic_bytes_per_launch": bytes_sweep,
+                "hbm_achieved_gbs": bytes_sweep / sweep_s / 1e9, "hbm_peak_gbs": hbm,
+                "hbm_frac": bytes_sweep / sweep_s / 1e9 / hbm, "hbm_peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, n_s, dt = oracle_rate(t, st, w, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one full oracle iteration on {n_s} entries drawn from the workload ({dt:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
+        "config": workload_config(w, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                      "l2": "inputs larger than L2 (CSR per mode %.0f MB > 129 MB)" %
+                                            ((N - 1) * 4 * nnz / 1e6 + s * nnz / 1e6),
+                                      "step": "factor sweep (all modes) + core sweep + loss + responsibility + "
+                                              "prune (pr=0)"}),
+        "op_ms": op_ms,
+        "sweep_only": {"value": world * units_per_step / sweep_s, "unit": UNIT},
+        "final_loss": {"sq_err": final_loss[0], "objective": final_loss[3], "re": final_loss[4]},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": args.e2e_steps, "includes": "H2D of idx+val, vest_build_index, one step, D2H of the loss"},
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

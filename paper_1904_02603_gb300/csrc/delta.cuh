@@ -1,0 +1,226 @@
+// delta_alpha^(n) (Eq. 11) on the GPU: the core permuted for mode n into a
+// [outer][j_f][JN] layout (j_n contiguous, padded to the bucket width JN with
+// zeros), then one staged contraction per observed entry with the other
+// modes' factor rows.  "f" is the lowest-numbered mode other than n; the
+// remaining other modes ("slow" modes) are folded into one weight per outer
+// index.  Outer slices whose core fibres are all zero are skipped uniformly.
+#pragma once
+
+#include "vest_internal.cuh"
+
+namespace vest {
+
+// Mode roles for a sweep of mode n.
+struct ModeRoles {
+  int n, f;                  // updated mode, fastest other mode (-1 if order 1)
+  int nslow;                 // number of slow modes
+  int slow[kMaxOrder];       // slow modes, fastest first
+  int Jn, Jf;
+  int Js[kMaxOrder];         // ranks of the slow modes
+  int64_t n_outer;           // prod of slow ranks
+  int64_t stride[kMaxOrder]; // core linear strides of every mode
+};
+
+inline ModeRoles mode_roles(const int32_t* J, int N, int n) {
+  ModeRoles r{};
+  r.n = n;
+  r.Jn = J[n];
+  int64_t s = 1;
+  for (int k = 0; k < N; ++k) {
+    r.stride[k] = s;
+    s *= J[k];
+  }
+  int q = 0;
+  r.f = -1;
+  for (int k = 0; k < N; ++k) {
+    if (k == n) continue;
+    if (r.f < 0) {
+      r.f = k;
+      r.Jf = J[k];
+    } else {
+      r.slow[q] = k;
+      r.Js[q] = J[k];
+      ++q;
+    }
+  }
+  r.nslow = q;
+  r.n_outer = 1;
+  for (int i = 0; i < q; ++i) r.n_outer *= r.Js[i];
+  return r;
+}
+
+// JN bucket widths instantiated by the kernels.
+inline int jn_bucket(int J) {
+  if (J <= 4) return 4;
+  if (J <= 8) return 8;
+  if (J <= 10) return 10;
+  if (J <= 12) return 12;
+  if (J <= 16) return 16;
+  return 32;
+}
+
+// Permuted, padded core for mode n: gp[(o * Jf + cf) * JN + j] = G[lin(j_n=j, j_f=cf, slow digits of o)],
+// zero for j >= Jn; onz[o] = 1 iff the outer slice o holds a nonzero.
+template <typename T>
+__global__ void prep_core_kernel(const T* __restrict__ G, ModeRoles r, int JN, T* __restrict__ gp,
+                                 uint8_t* __restrict__ onz) {
+  const int64_t slice = (int64_t)r.Jf * JN;
+  for (int64_t o = blockIdx.x; o < r.n_outer; o += gridDim.x) {
+    int64_t base = 0, rem = o;
+    for (int i = 0; i < r.nslow; ++i) {
+      base += (rem % r.Js[i]) * r.stride[r.slow[i]];
+      rem /= r.Js[i];
+    }
+    int any = 0;
+    for (int64_t e = threadIdx.x; e < slice; e += blockDim.x) {
+      const int cf = (int)(e / JN), j = (int)(e % JN);
+      T v = T(0);
+      if (j < r.Jn) v = G[base + (int64_t)cf * r.stride[r.f] + (int64_t)j * r.stride[r.n]];
+      gp[o * slice + e] = v;
+      any |= (v != T(0));
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) onz[o] = (uint8_t)any;
+  }
+}
+
+// ---------------------------------------------------------------- vector loads of JN core values
+template <typename T, int JN>
+__device__ __forceinline__ void fma_row(T (&d)[JN], T w, const T* __restrict__ g) {
+  if constexpr (sizeof(T) == 4 && JN % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < JN; j += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(g + j);
+      d[j + 0] = fmaf(w, v.x, d[j + 0]);
+      d[j + 1] = fmaf(w, v.y, d[j + 1]);
+      d[j + 2] = fmaf(w, v.z, d[j + 2]);
+      d[j + 3] = fmaf(w, v.w, d[j + 3]);
+    }
+  } else if constexpr (sizeof(T) == 4 && JN % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < JN; j += 2) {
+      const float2 v = *reinterpret_cast<const float2*>(g + j);
+      d[j + 0] = fmaf(w, v.x, d[j + 0]);
+      d[j + 1] = fmaf(w, v.y, d[j + 1]);
+    }
+  } else if constexpr (sizeof(T) == 8 && JN % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < JN; j += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(g + j);
+      d[j + 0] = fma(w, v.x, d[j + 0]);
+      d[j + 1] = fma(w, v.y, d[j + 1]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < JN; ++j) d[j] = d[j] + w * g[j];
+  }
+}
+
+// Slow-mode row pointers and ranks for one entry.
+struct SlowRows {
+  const void* row[kMaxOrder];
+  int J[kMaxOrder];
+};
+
+// delta for one entry.  NSLOW = number of slow modes when fixed at compile
+// time (0, 1, 2), or -1 for a runtime count.
+template <typename T, int JN, int NSLOW>
+__device__ __forceinline__ void compute_delta(T (&d)[JN], const T* __restrict__ g, const uint8_t* __restrict__ onz,
+                                              int64_t n_outer, int Jf, const T* __restrict__ rowf,
+                                              const SlowRows& sr, int nslow) {
+#pragma unroll
+  for (int j = 0; j < JN; ++j) d[j] = T(0);
+  const int64_t slice = (int64_t)Jf * JN;
+  if constexpr (NSLOW == 0) {
+    for (int cf = 0; cf < Jf; ++cf) fma_row<T, JN>(d, __ldg(rowf + cf), g + cf * JN);
+  } else if constexpr (NSLOW == 1) {
+    const T* r0 = static_cast<const T*>(sr.row[0]);
+    for (int o = 0; o < (int)n_outer; ++o) {
+      if (!onz[o]) continue;
+      const T w = __ldg(r0 + o);
+      if (w == T(0)) continue;
+      const T* go = g + o * slice;
+      for (int cf = 0; cf < Jf; ++cf) fma_row<T, JN>(d, w * __ldg(rowf + cf), go + cf * JN);
+    }
+  } else if constexpr (NSLOW == 2) {
+    const T* r0 = static_cast<const T*>(sr.row[0]);
+    const T* r1 = static_cast<const T*>(sr.row[1]);
+    const int J0 = sr.J[0], J1 = sr.J[1];
+    for (int d1 = 0; d1 < J1; ++d1) {
+      const T w1 = __ldg(r1 + d1);
+      if (w1 == T(0)) continue;
+      for (int d0 = 0; d0 < J0; ++d0) {
+        const int o = d0 + J0 * d1;
+        if (!onz[o]) continue;
+        const T w = w1 * __ldg(r0 + d0);
+        if (w == T(0)) continue;
+        const T* go = g + o * slice;
+        for (int cf = 0; cf < Jf; ++cf) fma_row<T, JN>(d, w * __ldg(rowf + cf), go + cf * JN);
+      }
+    }
+  } else {
+    int dig[kMaxOrder];
+    for (int i = 0; i < nslow; ++i) dig[i] = 0;
+    for (int64_t o = 0; o < n_outer; ++o) {
+      if (onz[o]) {
+        T w = T(1);
+        for (int i = 0; i < nslow; ++i) w *= __ldg(static_cast<const T*>(sr.row[i]) + dig[i]);
+        if (w != T(0)) {
+          const T* go = g + o * slice;
+          for (int cf = 0; cf < Jf; ++cf) fma_row<T, JN>(d, w * __ldg(rowf + cf), go + cf * JN);
+        }
+      }
+      for (int i = 0; i < nslow; ++i) {  // odometer, slow[0] fastest
+        if (++dig[i] < sr.J[i]) break;
+        dig[i] = 0;
+      }
+    }
+  }
+}
+
+// Row pointers of the other modes for the entry at CSR position p of mode n.
+// oidx rows are the other modes in ascending order: f first, then the slow ones.
+template <typename T>
+__device__ __forceinline__ const T* gather_rows(const DevModel<T>& M, const ModeRoles& r, const int32_t* __restrict__ oidx,
+                                                int64_t nnz, int64_t p, SlowRows& sr) {
+  const int64_t i_f = oidx[p];
+  for (int i = 0; i < r.nslow; ++i) {
+    const int k = r.slow[i];
+    const int64_t ik = oidx[(int64_t)(i + 1) * nnz + p];
+    sr.row[i] = M.A[k] + ik * M.J[k];
+    sr.J[i] = M.J[k];
+  }
+  return M.A[r.f] + i_f * M.J[r.f];
+}
+
+// ---------------------------------------------------------------- task -> rows
+// A task is a contiguous range [t0, t1) of positions in a mode's CSR order.
+// loads nzptr[k0 .. k1+1] into sptr; returns the number of rows overlapping it.
+__device__ __forceinline__ int load_task_rows(const int64_t* __restrict__ nzptr, int R, int64_t t0, int64_t t1,
+                                              int64_t* sptr, int64_t* sk0) {
+  __shared__ int64_t k_range[2];
+  if (threadIdx.x == 0) {
+    k_range[0] = upper_bound_m1(nzptr, (int64_t)R, t0);
+    k_range[1] = upper_bound_m1(nzptr, (int64_t)R, t1 - 1);
+  }
+  __syncthreads();
+  const int64_t k0 = k_range[0];
+  const int nrows = (int)(k_range[1] - k0 + 1);
+  for (int i = threadIdx.x; i <= nrows; i += blockDim.x) sptr[i] = nzptr[k0 + i];
+  *sk0 = k0;
+  __syncthreads();
+  return nrows;
+}
+
+// local row of position p: largest q < nrows with sptr[q] <= p
+__device__ __forceinline__ int local_row(const int64_t* sptr, int nrows, int64_t p) {
+  int lo = 0, hi = nrows - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (sptr[mid] <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace vest

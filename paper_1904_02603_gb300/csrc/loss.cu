@@ -1,0 +1,357 @@
+// Loss / RE (Eq. 1, Eq. 2, Eq. 4), entry-wise reconstruction (Eq. 7),
+// column normalisation (Algorithm 2, last loop) and zero counts.
+//
+// B(alpha) = sum_j a0[i_0, j] delta^(0)_alpha(j): the mode-0 delta of Eq. 11
+// dotted with the entry's mode-0 factor row, over the mode-0 CSR.  Products and
+// delta run in the storage type; r^2 and X^2 are summed in FP64 per thread, then
+// per thread block in a fixed shuffle tree, then across a fixed number of thread
+// blocks in a fixed order, so the loss is bitwise reproducible.
+#include <algorithm>
+
+#include "delta.cuh"
+
+namespace vest {
+
+constexpr int kLossTask = 256;
+constexpr int kLossCtas = 592;
+constexpr int kRegCtas = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// deterministic block sum; all threads must call; result valid in thread 0
+__device__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) t += sh[w];
+  __syncthreads();
+  return t;
+}
+
+struct LossArgs {
+  ModeRoles r;
+  int64_t ntasks;
+  const uint8_t* onz;
+  int use_smem_core;
+  double* part;  // [ctas][2]
+};
+
+template <typename T, int JN, int NSLOW>
+__global__ void __launch_bounds__(kLossTask) loss_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ gcore,
+                                                         LossArgs a, T* __restrict__ resid_csr0,
+                                                         T* __restrict__ resid_coo) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  const ModeRoles& r = a.r;
+  const int64_t core_elems = r.n_outer * r.Jf * JN;
+  T* sG = reinterpret_cast<T*>(smem_raw);
+  size_t off = a.use_smem_core ? (size_t)core_elems * sizeof(T) : 0;
+  off = (off + 15) & ~(size_t)15;
+  int64_t* sptr = reinterpret_cast<int64_t*>(smem_raw + off);
+  const T* g = gcore;
+  if (a.use_smem_core) {
+    for (int64_t e = threadIdx.x; e < core_elems; e += blockDim.x) sG[e] = gcore[e];
+    g = sG;
+  }
+  const int R = *csr.nnzrows;
+  const int64_t nnz = csr.nnz;
+  const int J0 = M.J[0];
+  double sq = 0.0, xx = 0.0;
+  __syncthreads();
+  for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
+    const int64_t t0 = task * kLossTask, t1 = min(t0 + (int64_t)kLossTask, nnz);
+    int64_t k0;
+    const int nrows = load_task_rows(csr.nzptr, R, t0, t1, sptr, &k0);
+    const int64_t p = t0 + threadIdx.x;
+    if (p < t1) {
+      const int lr = local_row(sptr, nrows, p);
+      const int64_t i0 = csr.nzrow[k0 + lr];
+      SlowRows sr;
+      const T* rowf = gather_rows<T>(M, r, csr.oidx, nnz, p, sr);
+      T d[JN];
+      compute_delta<T, JN, NSLOW>(d, g, a.onz, r.n_outer, r.Jf, rowf, sr, r.nslow);
+      const T* a0 = M.A[0] + i0 * J0;
+      T b = T(0);
+#pragma unroll
+      for (int j = 0; j < JN; ++j)
+        if (j < J0) b += __ldg(a0 + j) * d[j];
+      const T x = csr.val[p];
+      const T res = x - b;
+      if (resid_csr0) resid_csr0[p] = res;
+      if (resid_coo) resid_coo[csr.perm[p]] = res;
+      sq += (double)res * (double)res;
+      xx += (double)x * (double)x;
+    }
+    __syncthreads();
+  }
+  const double s1 = block_sum(sq, red);
+  const double s2 = block_sum(xx, red);
+  if (threadIdx.x == 0) {
+    a.part[blockIdx.x * 2 + 0] = s1;
+    a.part[blockIdx.x * 2 + 1] = s2;
+  }
+}
+
+// regulariser partial sums over every factor and core element
+template <typename T>
+__global__ void reg_kernel(DevModel<T> M, int reg, double* __restrict__ part) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int seg = 0; seg <= M.N; ++seg) {
+    const T* v = seg < M.N ? M.A[seg] : M.G;
+    const int64_t size = seg < M.N ? M.I[seg] * M.J[seg] : M.gsize;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < size; e += (int64_t)gridDim.x * blockDim.x) {
+      const double x = (double)v[e];
+      acc += reg == VEST_REG_L1 ? fabs(x) : x * x;
+    }
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void loss_final_kernel(const double* __restrict__ lpart, int nl, const double* __restrict__ rpart, int nr,
+                                  double lambda, double* __restrict__ out) {
+  __shared__ double red[32];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+    a += lpart[2 * i];
+    b += lpart[2 * i + 1];
+  }
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) c += rpart[i];
+  const double sq = block_sum(a, red);
+  const double xx = block_sum(b, red);
+  const double rg = block_sum(c, red);
+  if (threadIdx.x == 0) {
+    out[0] = sq;
+    out[1] = xx;
+    out[2] = lambda * rg;
+    out[3] = sq + lambda * rg;
+    out[4] = xx > 0.0 ? sqrt(sq) / sqrt(xx) : 0.0;
+  }
+}
+
+constexpr size_t kLossSmemBudget = 160 * 1024;
+
+template <typename T, int JN, int NSLOW>
+static vest_status launch_loss(const DevModel<T>& M, const DevMode<T>& csr, const T* gp, const LossArgs& a,
+                               size_t smem, int grid, T* r0, T* rc, cudaStream_t s) {
+  auto kern = loss_kernel<T, JN, NSLOW>;
+  VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, kLossTask, smem, s>>>(M, csr, gp, a, r0, rc);
+  VEST_LAUNCH("loss_kernel");
+  return VEST_OK;
+}
+
+template <typename T, int JN>
+static vest_status loss_nslow(int nslow, const DevModel<T>& M, const DevMode<T>& csr, const T* gp, const LossArgs& a,
+                              size_t smem, int grid, T* r0, T* rc, cudaStream_t s) {
+  if (nslow == 1) return launch_loss<T, JN, 1>(M, csr, gp, a, smem, grid, r0, rc, s);
+  if (nslow == 2) return launch_loss<T, JN, 2>(M, csr, gp, a, smem, grid, r0, rc, s);
+  return launch_loss<T, JN, -1>(M, csr, gp, a, smem, grid, r0, rc, s);
+}
+
+template <typename T>
+vest_status loss_impl(const vest_index* ix, const vest_model* m, int reg, double lambda, double* out, T* resid_csr0,
+                      T* resid_coo, char* scratch, const ScratchPlan& plan, cudaStream_t s) {
+  const DevModel<T> M = dev_model<T>(m);
+  const ModeRoles r = mode_roles(M.J, M.N, 0);
+  const int JN = jn_bucket(r.Jn);
+  const int64_t core_elems = r.n_outer * r.Jf * JN;
+  T* gp = reinterpret_cast<T*>(scratch + plan.off_gperm);
+  uint8_t* onz = reinterpret_cast<uint8_t*>(scratch + plan.off_gperm + align_up((size_t)core_elems * sizeof(T)));
+  if (align_up((size_t)core_elems * sizeof(T)) + align_up((size_t)r.n_outer) > plan.gperm_bytes)
+    return fail(VEST_ERR_WORKSPACE, "scratch region for the permuted core too small");
+  prep_core_kernel<T><<<(unsigned)std::min<int64_t>(r.n_outer, 4096), 128, 0, s>>>(M.G, r, JN, gp, onz);
+  VEST_LAUNCH("prep_core_kernel");
+  LossArgs a{};
+  a.r = r;
+  a.onz = onz;
+  a.ntasks = ceil_div(ix->nnz, kLossTask);
+  const size_t core_bytes = align_up((size_t)core_elems * sizeof(T), 16);
+  a.use_smem_core = core_bytes + (kLossTask + 2) * 8 <= kLossSmemBudget;
+  const size_t smem = (a.use_smem_core ? core_bytes : 0) + (kLossTask + 2) * 8;
+  double* lpart = reinterpret_cast<double*>(scratch + plan.off_part);
+  double* rpart = lpart + 2 * kLossCtas;
+  a.part = lpart;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.ntasks, kLossCtas));
+  if (ix->nnz > 0) {
+    const DevMode<T> csr = dev_mode<T>(ix, 0);
+    switch (JN) {
+      case 4: VEST_TRY((loss_nslow<T, 4>(r.nslow, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
+      case 8: VEST_TRY((loss_nslow<T, 8>(r.nslow, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
+      case 10: VEST_TRY((loss_nslow<T, 10>(r.nslow, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
+      case 12: VEST_TRY((loss_nslow<T, 12>(r.nslow, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
+      case 16: VEST_TRY((loss_nslow<T, 16>(r.nslow, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
+      default: VEST_TRY((loss_nslow<T, 32>(r.nslow, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
+    }
+  }
+  reg_kernel<T><<<kRegCtas, 256, 0, s>>>(M, reg, rpart);
+  VEST_LAUNCH("reg_kernel");
+  loss_final_kernel<<<1, 256, 0, s>>>(lpart, ix->nnz > 0 ? grid : 0, rpart, kRegCtas, lambda, out);
+  VEST_LAUNCH("loss_final_kernel");
+  return VEST_OK;
+}
+
+size_t loss_part_bytes() { return (size_t)(2 * kLossCtas + kRegCtas) * 8; }
+
+template vest_status loss_impl<float>(const vest_index*, const vest_model*, int, double, double*, float*, float*, char*,
+                                      const ScratchPlan&, cudaStream_t);
+template vest_status loss_impl<double>(const vest_index*, const vest_model*, int, double, double*, double*, double*,
+                                       char*, const ScratchPlan&, cudaStream_t);
+
+// ------------------------------------------------------------------ completion queries (Eq. 7)
+template <typename T>
+__global__ void reconstruct_kernel(DevModel<T> M, const int32_t* __restrict__ q, int64_t count, T* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    // B = sum over core elements, staged: fold the slowest mode first
+    T acc = T(0);
+    int64_t lin = 0;
+    const int64_t gs = M.gsize;
+    int dig[kMaxOrder];
+    for (int n = 0; n < M.N; ++n) dig[n] = 0;
+    for (lin = 0; lin < gs; ++lin) {
+      T p = M.G[lin];
+      if (p != T(0)) {
+        for (int n = 0; n < M.N; ++n) p *= M.A[n][(int64_t)q[(int64_t)n * count + i] * M.J[n] + dig[n]];
+        acc += p;
+      }
+      for (int n = 0; n < M.N; ++n) {
+        if (++dig[n] < M.J[n]) break;
+        dig[n] = 0;
+      }
+    }
+    out[i] = acc;
+  }
+}
+
+template <typename T>
+vest_status reconstruct_impl(const vest_model* m, const int32_t* q_idx, int64_t count, T* out, cudaStream_t s) {
+  if (count <= 0) return VEST_OK;
+  const DevModel<T> M = dev_model<T>(m);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(count, 256), (int64_t)num_sms() * 8));
+  reconstruct_kernel<T><<<grid, 256, 0, s>>>(M, q_idx, count, out);
+  VEST_LAUNCH("reconstruct_kernel");
+  return VEST_OK;
+}
+template vest_status reconstruct_impl<float>(const vest_model*, const int32_t*, int64_t, float*, cudaStream_t);
+template vest_status reconstruct_impl<double>(const vest_model*, const int32_t*, int64_t, double*, cudaStream_t);
+
+// ------------------------------------------------------------------ normalisation
+constexpr int kNormCtas = 128;
+
+template <typename T>
+__global__ void colnorm_partial_kernel(const T* __restrict__ A, int64_t I, int J, double* __restrict__ part) {
+  __shared__ double sh[256];
+  const int per = blockDim.x / J;  // threads per column group
+  const int j = threadIdx.x % J, rl = threadIdx.x / J;
+  double acc = 0.0;
+  if (rl < per) {
+    const int64_t rows_per_cta = ceil_div(I, (int64_t)gridDim.x);
+    const int64_t r0 = blockIdx.x * rows_per_cta, r1 = min(I, r0 + rows_per_cta);
+    for (int64_t i = r0 + rl; i < r1; i += per) {
+      const double x = (double)A[i * J + j];
+      acc += x * x;
+    }
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < J) {
+    double t = 0.0;
+    for (int q = 0; q < per; ++q) t += sh[q * J + threadIdx.x];
+    part[blockIdx.x * J + threadIdx.x] = t;
+  }
+}
+
+__global__ void colnorm_final_kernel(const double* __restrict__ part, int nctas, int J, double* __restrict__ b) {
+  const int j = threadIdx.x;
+  if (j < J) {
+    double t = 0.0;
+    for (int c = 0; c < nctas; ++c) t += part[c * J + j];
+    b[j] = sqrt(t);
+  }
+}
+
+template <typename T>
+__global__ void scale_columns_kernel(T* __restrict__ A, int64_t I, int J, const double* __restrict__ b) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < I * J; e += (int64_t)gridDim.x * blockDim.x) {
+    const double bj = b[e % J];
+    if (bj > 0.0) A[e] = (T)((double)A[e] / bj);
+  }
+}
+
+template <typename T>
+__global__ void scale_core_kernel(DevModel<T> M, const double* __restrict__ b /* [N][32] */) {
+  for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < M.gsize; lin += (int64_t)gridDim.x * blockDim.x) {
+    double g = (double)M.G[lin];
+    int64_t rem = lin;
+    for (int n = 0; n < M.N; ++n) {
+      const int jn = (int)(rem % M.J[n]);
+      rem /= M.J[n];
+      g = (double)(T)(g * b[n * kMaxRank + jn]);
+    }
+    M.G[lin] = (T)g;
+  }
+}
+
+template <typename T>
+vest_status normalize_impl(const vest_model* m, char* scratch, cudaStream_t s) {
+  const DevModel<T> M = dev_model<T>(m);
+  double* part = reinterpret_cast<double*>(scratch);
+  double* b = part + (size_t)kNormCtas * kMaxRank;
+  for (int n = 0; n < M.N; ++n) {
+    const int J = M.J[n];
+    const int threads = std::max(J, 256 / J * J);
+    colnorm_partial_kernel<T><<<kNormCtas, threads, 0, s>>>(M.A[n], M.I[n], J, part);
+    VEST_LAUNCH("colnorm_partial");
+    colnorm_final_kernel<<<1, 32, 0, s>>>(part, kNormCtas, J, b + n * kMaxRank);
+    VEST_LAUNCH("colnorm_final");
+    const int grid = std::max(1, std::min<int>((int)ceil_div(M.I[n] * J, 256), num_sms() * 8));
+    scale_columns_kernel<T><<<grid, 256, 0, s>>>(M.A[n], M.I[n], J, b + n * kMaxRank);
+    VEST_LAUNCH("scale_columns");
+  }
+  const int grid = std::max(1, std::min<int>((int)ceil_div(M.gsize, 256), num_sms() * 8));
+  scale_core_kernel<T><<<grid, 256, 0, s>>>(M, b);
+  VEST_LAUNCH("scale_core");
+  return VEST_OK;
+}
+template vest_status normalize_impl<float>(const vest_model*, char*, cudaStream_t);
+template vest_status normalize_impl<double>(const vest_model*, char*, cudaStream_t);
+
+size_t normalize_scratch_bytes() { return (size_t)(kNormCtas + kMaxOrder) * kMaxRank * 8; }
+
+// ------------------------------------------------------------------ zero counts
+template <typename T>
+__global__ void count_zeros_kernel(DevModel<T> M, unsigned long long* __restrict__ out) {
+  for (int seg = 0; seg <= M.N; ++seg) {
+    const T* v = seg < M.N ? M.A[seg] : M.G;
+    const int64_t size = seg < M.N ? M.I[seg] * M.J[seg] : M.gsize;
+    unsigned long long c = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < size; e += (int64_t)gridDim.x * blockDim.x)
+      c += (v[e] == T(0));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out + seg, c);
+  }
+}
+
+template <typename T>
+vest_status count_zeros_impl(const vest_model* m, int64_t* out, char* scratch, cudaStream_t s) {
+  (void)scratch;
+  const DevModel<T> M = dev_model<T>(m);
+  VEST_CUDA(cudaMemsetAsync(out, 0, (size_t)(M.N + 1) * 8, s));
+  count_zeros_kernel<T><<<num_sms() * 2, 256, 0, s>>>(M, reinterpret_cast<unsigned long long*>(out));
+  VEST_LAUNCH("count_zeros");
+  return VEST_OK;
+}
+template vest_status count_zeros_impl<float>(const vest_model*, int64_t*, char*, cudaStream_t);
+template vest_status count_zeros_impl<double>(const vest_model*, int64_t*, char*, cudaStream_t);
+
+}  // namespace vest

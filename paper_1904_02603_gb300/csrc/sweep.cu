@@ -1,0 +1,399 @@
+// Factor sweep (Algorithm 4; Lemma 1, Eq. 9-11; Lemma 3, Eq. 13) and the
+// factor part of the responsibility (Eq. 6, Algorithm 3) over the mode-n CSR.
+//
+// Work is cut into tasks of TASK consecutive CSR positions (nnz-balanced, so
+// heavy Zipf rows and one-entry rows cost the same per entry):
+//   phase 1  one thread per entry: delta_alpha (Eq. 11) into shared memory;
+//   phase 2  one warp per row piece, lanes over outputs: the row sums
+//            c_j = sum X delta_j and V_jt = sum delta_j delta_t (Eq. 10) for the
+//            update, or sum r delta_j and sum delta_j^2 for the responsibility,
+//            summed over the piece in CSR order (accumulator: T);
+//   phase 3  one thread per row: rows that lie inside the task are finished
+//            at once (sequential CD over j, FP64); a row cut by a task edge
+//            writes its piece to a spill slot, and the task where the row
+//            starts registers it for the fix-up kernel, which adds the pieces
+//            in task order in FP64 and finishes the row.
+// Rows of A^(n) are independent (delta does not involve A^(n)), so finishing
+// them while other tasks run is safe.
+#include <algorithm>
+
+#include "delta.cuh"
+
+namespace vest {
+
+enum { kModeUpdate = 0, kModeResp = 1 };
+
+template <typename T>
+struct AccOf {
+  using type = T;
+};
+
+struct SweepArgs {
+  ModeRoles r;
+  int reg;
+  double lambda;
+  int64_t ntasks;
+  int task;
+  int P;
+  int use_smem_core;
+  const uint8_t* onz;
+  double* spill;       // [ntasks][2][P]
+  int32_t* spanning;   // [ntasks]
+  // responsibility
+  const void* resid_coo;
+  const double* stats;  // device {.., x_norm2 at [1], .., RE at [4]}
+  double* delta;        // I_n x J_n
+  double* resp;         // nullable
+};
+
+__host__ __device__ inline int packed_row(int j, int Jn) { return j * Jn - (j * (j - 1)) / 2; }
+
+// Finish a row from its sums (FP64).  kModeUpdate: sequential CD over j (Eq. 9
+// or Eq. 13 with g = -2(c_j - sum_{t!=j} V_jt a_t), d = 2 V_jj), each new value
+// rounded to the storage type before the next j uses it.  kModeResp: Delta and
+// Resp per element (Eq. 3, 6).
+template <typename T, typename S, int MODE>
+__device__ void finish_row(const DevModel<T>& M, int n, int64_t row, const S* sums, const SweepArgs& a) {
+  const int Jn = M.J[n];
+  T* arow = M.A[n] + row * Jn;
+  if constexpr (MODE == kModeUpdate) {
+    const uint8_t* mrow = M.mask[n] + row * Jn;
+    double av[kMaxRank];
+    for (int t = 0; t < Jn; ++t) av[t] = (double)arow[t];
+    for (int j = 0; j < Jn; ++j) {
+      if (mrow[j]) continue;
+      double num = (double)sums[j];
+      for (int t = 0; t < Jn; ++t) {
+        if (t == j) continue;
+        const int lo = t < j ? t : j, hi = t < j ? j : t;
+        num -= (double)sums[Jn + packed_row(lo, Jn) + (hi - lo)] * av[t];
+      }
+      const double vjj = (double)sums[Jn + packed_row(j, Jn)];
+      double nv;
+      if (a.reg == VEST_REG_L1) {
+        const double g = -2.0 * num, d = 2.0 * vjj;
+        nv = g > a.lambda ? (a.lambda - g) / d : (g < -a.lambda ? -(a.lambda + g) / d : 0.0);
+      } else {
+        nv = num / (vjj + a.lambda);
+      }
+      const T st = (T)nv;
+      arow[j] = st;
+      av[j] = (double)st;
+    }
+  } else {
+    const double xx = a.stats[1], re = a.stats[4];
+    for (int j = 0; j < Jn; ++j) {
+      const double aij = (double)arow[j];
+      const double dl = 2.0 * aij * (double)sums[j] + aij * aij * (double)sums[Jn + j];
+      a.delta[row * Jn + j] = dl;
+      if (a.resp) a.resp[row * Jn + j] = re > 0.0 ? (sqrt(fmax(re * re + dl / xx, 0.0)) - re) / re : 0.0;
+    }
+  }
+}
+
+template <typename T, int JN, int NSLOW, int MODE>
+__global__ void __launch_bounds__(256) sweep_task_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ gcore,
+                                                         SweepArgs a) {
+  using S = typename AccOf<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ModeRoles& r = a.r;
+  const int TASK = a.task;
+  const int JNS = JN + 1;
+  const int P = a.P;
+  const int64_t core_elems = r.n_outer * r.Jf * JN;
+  // shared layout: core | sptr | D | X | acc
+  T* sG = reinterpret_cast<T*>(smem_raw);
+  size_t off = a.use_smem_core ? (size_t)core_elems * sizeof(T) : 0;
+  off = (off + 15) & ~(size_t)15;
+  int64_t* sptr = reinterpret_cast<int64_t*>(smem_raw + off);
+  off += (size_t)(TASK + 2) * 8;
+  T* sD = reinterpret_cast<T*>(smem_raw + off);
+  off += (size_t)TASK * JNS * sizeof(T);
+  T* sX = reinterpret_cast<T*>(smem_raw + off);
+  off += (size_t)TASK * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  S* sAcc = reinterpret_cast<S*>(smem_raw + off);
+
+  const T* g = gcore;
+  if (a.use_smem_core) {
+    for (int64_t e = threadIdx.x; e < core_elems; e += blockDim.x) sG[e] = gcore[e];
+    g = sG;
+  }
+  const int R = *csr.nnzrows;
+  const int64_t nnz = csr.nnz;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int n = r.n;
+  const int Jn = r.Jn;
+  __syncthreads();
+
+  for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
+    const int64_t t0 = task * TASK, t1 = min(t0 + (int64_t)TASK, nnz);
+    const int cnt = (int)(t1 - t0);
+    int64_t k0;
+    const int nrows = load_task_rows(csr.nzptr, R, t0, t1, sptr, &k0);
+
+    // phase 1: delta per entry
+    if ((int)threadIdx.x < cnt) {
+      const int64_t p = t0 + threadIdx.x;
+      SlowRows sr;
+      const T* rowf = gather_rows<T>(M, r, csr.oidx, nnz, p, sr);
+      T d[JN];
+      compute_delta<T, JN, NSLOW>(d, g, a.onz, r.n_outer, r.Jf, rowf, sr, r.nslow);
+      T* dst = sD + threadIdx.x * JNS;
+#pragma unroll
+      for (int j = 0; j < JN; ++j) dst[j] = d[j];
+      if constexpr (MODE == kModeUpdate) sX[threadIdx.x] = csr.val[p];
+      else sX[threadIdx.x] = static_cast<const T*>(a.resid_coo)[csr.perm[p]];
+    }
+    __syncthreads();
+
+    // phase 2: per-row sums over the task's piece of the row
+    for (int k = warp; k < nrows; k += nwarps) {
+      const int s = (int)(max(sptr[k], t0) - t0), e = (int)(min(sptr[k + 1], t1) - t0);
+      for (int pi = lane; pi < P; pi += 32) {
+        S acc = S(0);
+        if (pi < Jn) {
+          for (int q = s; q < e; ++q) acc += (S)sX[q] * (S)sD[q * JNS + pi];
+        } else if constexpr (MODE == kModeUpdate) {
+          int u = pi - Jn, j = 0;
+          while (u >= Jn - j) {
+            u -= Jn - j;
+            ++j;
+          }
+          const int t = j + u;
+          for (int q = s; q < e; ++q) acc += (S)sD[q * JNS + j] * (S)sD[q * JNS + t];
+        } else {
+          const int j = pi - Jn;
+          for (int q = s; q < e; ++q) acc += (S)sD[q * JNS + j] * (S)sD[q * JNS + j];
+        }
+        sAcc[k * P + pi] = acc;
+      }
+    }
+    __syncthreads();
+
+    // phase 3: finish whole rows, spill cut ones
+    for (int k = threadIdx.x; k < nrows; k += blockDim.x) {
+      const int64_t rs = sptr[k], re = sptr[k + 1];
+      if (rs >= t0 && re <= t1) {
+        finish_row<T, S, MODE>(M, n, (int64_t)csr.nzrow[k0 + k], sAcc + k * P, a);
+      } else {
+        const int slot = (k == 0) ? 0 : 1;
+        double* sp = a.spill + ((size_t)task * 2 + slot) * P;
+        for (int i = 0; i < P; ++i) sp[i] = (double)sAcc[k * P + i];
+      }
+      if (k == nrows - 1) a.spanning[task] = (rs >= t0 && re > t1) ? (int32_t)(k0 + k) : -1;
+    }
+    __syncthreads();
+  }
+}
+
+// Rows cut by task edges: add the pieces in task order (FP64) and finish.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) sweep_fixup_kernel(DevModel<T> M, DevMode<T> csr, SweepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* part = reinterpret_cast<double*>(smem_raw);  // [groups][P]
+  const int P = a.P;
+  const int groups = max(1, (int)blockDim.x / P);
+  for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
+    const int32_t kg = a.spanning[task];
+    if (kg < 0) continue;  // uniform across the block
+    const int64_t rs = csr.nzptr[kg], re = csr.nzptr[kg + 1];
+    const int64_t tlast = (re - 1) / a.task;
+    const int first_slot = (rs == task * (int64_t)a.task) ? 0 : 1;
+    // groups > 1: thread (gi, pi) sums output pi over tasks gi, gi + groups, ...;
+    // groups == 1 (P > blockDim): each thread sums outputs threadIdx.x + k * blockDim over all tasks
+    const int gi = groups > 1 ? (int)threadIdx.x / P : 0;
+    const int pstart = groups > 1 ? (int)threadIdx.x % P : (int)threadIdx.x;
+    const int pstep = groups > 1 ? P : (int)blockDim.x;
+    if (gi < groups) {
+      for (int pp = pstart; pp < P; pp += pstep) {
+        double acc = 0.0;
+        for (int64_t tt = task + gi; tt <= tlast; tt += groups) {
+          const int slot = (tt == task) ? first_slot : 0;
+          acc += a.spill[((size_t)tt * 2 + slot) * P + pp];
+        }
+        part[gi * P + pp] = acc;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int pp = 0; pp < P; ++pp) {
+        double acc = 0.0;
+        for (int gg = 0; gg < groups; ++gg) acc += part[gg * P + pp];
+        part[pp] = acc;
+      }
+      finish_row<T, double, MODE>(M, a.r.n, (int64_t)csr.nzrow[kg], part, a);
+    }
+    __syncthreads();
+  }
+}
+
+// Rows with no observed entry: the update gives 0; their Delta is 0.
+template <typename T, int MODE>
+__global__ void empty_rows_kernel(DevModel<T> M, int n, const int64_t* __restrict__ row_ptr, double* delta,
+                                  double* resp) {
+  const int Jn = M.J[n];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M.I[n]; i += (int64_t)gridDim.x * blockDim.x) {
+    if (row_ptr[i] != row_ptr[i + 1]) continue;
+    for (int j = 0; j < Jn; ++j) {
+      if constexpr (MODE == kModeUpdate) {
+        M.A[n][i * Jn + j] = T(0);
+      } else {
+        delta[i * Jn + j] = 0.0;
+        if (resp) resp[i * Jn + j] = 0.0;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host side
+template <typename T>
+static int outputs_per_row(int Jn, int mode_kind) {
+  return mode_kind == kModeUpdate ? Jn + Jn * (Jn + 1) / 2 : 2 * Jn;
+}
+
+constexpr size_t kSmemBudget = 200 * 1024;
+
+template <typename T>
+static size_t task_smem(int task, int JN, int P, size_t core_bytes) {
+  size_t off = (core_bytes + 15) & ~(size_t)15;
+  off += (size_t)(task + 2) * 8;
+  off += (size_t)task * (JN + 1) * sizeof(T);
+  off += (size_t)task * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  off += (size_t)task * P * sizeof(typename AccOf<T>::type);
+  return off;
+}
+
+// Task size used for a mode: the largest of 256/128/64/32 whose shared memory fits
+// (the core is placed in shared memory only when it leaves room for >= 64-entry tasks).
+template <typename T>
+int sweep_task_size(int Jn, int P, int64_t core_elems, int* use_smem_core) {
+  const int JN = jn_bucket(Jn);
+  const size_t core_bytes = (size_t)core_elems * sizeof(T);
+  for (int pass = 0; pass < 2; ++pass) {
+    const size_t cb = pass == 0 ? core_bytes : 0;
+    for (int task = 256; task >= 32; task >>= 1) {
+      if (pass == 0 && task < 64) break;
+      if (task_smem<T>(task, JN, P, cb) <= kSmemBudget) {
+        *use_smem_core = pass == 0;
+        return task;
+      }
+    }
+  }
+  *use_smem_core = 0;
+  return 32;
+}
+
+template int sweep_task_size<float>(int, int, int64_t, int*);
+template int sweep_task_size<double>(int, int, int64_t, int*);
+
+template <typename T, int JN, int NSLOW, int MODE>
+static vest_status launch_task(const DevModel<T>& M, const DevMode<T>& csr, const T* gp, const SweepArgs& a,
+                               size_t smem, cudaStream_t s) {
+  auto kern = sweep_task_kernel<T, JN, NSLOW, MODE>;
+  VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t grid = std::min<int64_t>(a.ntasks, (int64_t)num_sms() * 16);
+  kern<<<(unsigned)std::max<int64_t>(grid, 1), a.task, smem, s>>>(M, csr, gp, a);
+  VEST_LAUNCH("sweep_task_kernel");
+  return VEST_OK;
+}
+
+template <typename T, int JN, int MODE>
+static vest_status dispatch_nslow(int nslow, const DevModel<T>& M, const DevMode<T>& csr, const T* gp,
+                                  const SweepArgs& a, size_t smem, cudaStream_t s) {
+  if (MODE == kModeUpdate && nslow == 1) return launch_task<T, JN, 1, MODE>(M, csr, gp, a, smem, s);
+  if (MODE == kModeUpdate && nslow == 2) return launch_task<T, JN, 2, MODE>(M, csr, gp, a, smem, s);
+  return launch_task<T, JN, -1, MODE>(M, csr, gp, a, smem, s);
+}
+
+template <typename T, int MODE>
+static vest_status dispatch_jn(int JN, int nslow, const DevModel<T>& M, const DevMode<T>& csr, const T* gp,
+                               const SweepArgs& a, size_t smem, cudaStream_t s) {
+  switch (JN) {
+    case 4: return dispatch_nslow<T, 4, MODE>(nslow, M, csr, gp, a, smem, s);
+    case 8: return dispatch_nslow<T, 8, MODE>(nslow, M, csr, gp, a, smem, s);
+    case 10: return dispatch_nslow<T, 10, MODE>(nslow, M, csr, gp, a, smem, s);
+    case 12: return dispatch_nslow<T, 12, MODE>(nslow, M, csr, gp, a, smem, s);
+    case 16: return dispatch_nslow<T, 16, MODE>(nslow, M, csr, gp, a, smem, s);
+    default: return dispatch_nslow<T, 32, MODE>(nslow, M, csr, gp, a, smem, s);
+  }
+}
+
+template <typename T, int MODE>
+static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, SweepArgs a, char* scratch,
+                            const ScratchPlan& plan, cudaStream_t s) {
+  const ModeRoles r = mode_roles(M.J, M.N, n);
+  a.r = r;
+  const int JN = jn_bucket(r.Jn);
+  T* gp = reinterpret_cast<T*>(scratch + plan.off_gperm);
+  const int64_t core_elems = r.n_outer * r.Jf * JN;
+  uint8_t* onz = reinterpret_cast<uint8_t*>(scratch + plan.off_gperm + align_up((size_t)core_elems * sizeof(T)));
+  if (align_up((size_t)core_elems * sizeof(T)) + align_up((size_t)r.n_outer) > plan.gperm_bytes)
+    return fail(VEST_ERR_WORKSPACE, "scratch region for the permuted core too small");
+  prep_core_kernel<T><<<(unsigned)std::min<int64_t>(r.n_outer, 4096), 128, 0, s>>>(M.G, r, JN, gp, onz);
+  VEST_LAUNCH("prep_core_kernel");
+  a.onz = onz;
+  a.P = outputs_per_row<T>(r.Jn, MODE);
+  int use_smem = 0;
+  a.task = sweep_task_size<T>(r.Jn, a.P, core_elems, &use_smem);
+  a.use_smem_core = use_smem;
+  a.ntasks = ceil_div(ix->nnz, a.task);
+  if ((size_t)a.ntasks * 2 * a.P * 8 > plan.spill_bytes || a.ntasks > plan.ntasks)
+    return fail(VEST_ERR_WORKSPACE, "scratch spill region too small");
+  a.spill = reinterpret_cast<double*>(scratch + plan.off_spill);
+  a.spanning = reinterpret_cast<int32_t*>(scratch + plan.off_spanning);
+  const DevMode<T> csr = dev_mode<T>(ix, n);
+  const int eg = std::max(1, std::min<int>((int)ceil_div(M.I[n], 256), num_sms() * 8));
+  empty_rows_kernel<T, MODE><<<eg, 256, 0, s>>>(M, n, ix->mode[n].row_ptr, a.delta, a.resp);
+  VEST_LAUNCH("empty_rows_kernel");
+  if (ix->nnz == 0) return VEST_OK;
+  const size_t smem = task_smem<T>(a.task, JN, a.P, use_smem ? (size_t)core_elems * sizeof(T) : 0);
+  VEST_TRY(dispatch_jn<T, MODE>(JN, r.nslow, M, csr, gp, a, smem, s));
+  const size_t fsmem = (size_t)std::max(1, 256 / a.P) * a.P * 8 + 8 * a.P;
+  auto fk = sweep_fixup_kernel<T, MODE>;
+  VEST_CUDA(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+  const int64_t fgrid = std::min<int64_t>(a.ntasks, (int64_t)num_sms() * 8);
+  fk<<<(unsigned)fgrid, 256, fsmem, s>>>(M, csr, a);
+  VEST_LAUNCH("sweep_fixup_kernel");
+  return VEST_OK;
+}
+
+template <typename T>
+vest_status sweep_factors_mode(const vest_index* ix, const vest_model* m, int reg, double lambda, int mode,
+                               char* scratch, const ScratchPlan& plan, cudaStream_t s) {
+  const DevModel<T> M = dev_model<T>(m);
+  SweepArgs a{};
+  a.reg = reg;
+  a.lambda = lambda;
+  return run_mode<T, kModeUpdate>(ix, M, mode, a, scratch, plan, s);
+}
+
+template <typename T>
+vest_status responsibility_factors(const vest_index* ix, const vest_model* m, const double* stats,
+                                   double* const* delta_factor, double* const* resp_factor, char* scratch,
+                                   const ScratchPlan& plan, cudaStream_t s) {
+  const DevModel<T> M = dev_model<T>(m);
+  for (int n = 0; n < M.N; ++n) {
+    SweepArgs a{};
+    a.resid_coo = scratch + plan.off_resid_coo;
+    a.stats = stats;
+    a.delta = delta_factor[n];
+    a.resp = resp_factor ? resp_factor[n] : nullptr;
+    VEST_TRY((run_mode<T, kModeResp>(ix, M, n, a, scratch, plan, s)));
+  }
+  return VEST_OK;
+}
+
+template vest_status sweep_factors_mode<float>(const vest_index*, const vest_model*, int, double, int, char*,
+                                               const ScratchPlan&, cudaStream_t);
+template vest_status sweep_factors_mode<double>(const vest_index*, const vest_model*, int, double, int, char*,
+                                                const ScratchPlan&, cudaStream_t);
+template vest_status responsibility_factors<float>(const vest_index*, const vest_model*, const double*,
+                                                   double* const*, double* const*, char*, const ScratchPlan&,
+                                                   cudaStream_t);
+template vest_status responsibility_factors<double>(const vest_index*, const vest_model*, const double*,
+                                                    double* const*, double* const*, char*, const ScratchPlan&,
+                                                    cudaStream_t);
+
+}  // namespace vest

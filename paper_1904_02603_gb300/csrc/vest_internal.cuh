@@ -1,0 +1,203 @@
+// Internal declarations shared by the libvest translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "vest.h"
+
+namespace vest {
+
+constexpr int kMaxOrder = VEST_MAX_ORDER;
+constexpr int kMaxRank = VEST_MAX_RANK;
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+vest_status fail(vest_status st, const std::string& msg);
+vest_status cuda_fail(cudaError_t e, const char* what);
+
+#define VEST_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e__ = (call);                             \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+  } while (0)
+
+// Every kernel launch site is followed by VEST_LAUNCH (or VEST_LAUNCH_N when
+// one check covers n launches): it checks the launch and counts it.
+void count_launches(int n);
+
+#define VEST_LAUNCH_N(what, n)                                 \
+  do {                                                         \
+    count_launches(n);                                         \
+    cudaError_t e__ = cudaGetLastError();                      \
+    if (e__ != cudaSuccess) return cuda_fail(e__, what);       \
+  } while (0)
+#define VEST_LAUNCH(what) VEST_LAUNCH_N(what, 1)
+
+#define VEST_TRY(...)                   \
+  do {                                  \
+    vest_status s__ = (__VA_ARGS__);    \
+    if (s__ != VEST_OK) return s__;     \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ------------------------------------------------------------------ index
+struct ModeIndex {
+  int64_t* row_ptr;  // [I_n + 1]
+  int32_t* perm;     // [nnz]
+  int32_t* oidx;     // [(N-1)][nnz], other modes ascending
+  void* val;         // [nnz]
+  int64_t* nzptr;    // [cap + 1]
+  int32_t* nzrow;    // [cap]
+  int32_t* nnzrows;  // device scalar R_n
+  int64_t cap;       // min(I_n, nnz)
+};
+
+}  // namespace vest
+
+struct vest_index {
+  int32_t order;
+  int32_t val_dtype;
+  int64_t dims[VEST_MAX_ORDER];
+  int64_t nnz;
+  vest::ModeIndex mode[VEST_MAX_ORDER];
+  size_t ws_bytes;
+};
+
+namespace vest {
+
+// ------------------------------------------------------------------ device views
+template <typename T>
+struct DevModel {
+  int32_t N;
+  int32_t J[kMaxOrder];
+  int64_t I[kMaxOrder];
+  T* A[kMaxOrder];
+  uint8_t* mask[kMaxOrder];
+  T* G;
+  uint8_t* Gmask;
+  int64_t gsize;
+};
+
+template <typename T>
+inline DevModel<T> dev_model(const vest_model* m) {
+  DevModel<T> d{};
+  d.N = m->order;
+  d.gsize = 1;
+  for (int n = 0; n < m->order; ++n) {
+    d.J[n] = m->ranks[n];
+    d.I[n] = m->dims[n];
+    d.A[n] = static_cast<T*>(m->factor[n]);
+    d.mask[n] = m->factor_mask[n];
+    d.gsize *= m->ranks[n];
+  }
+  d.G = static_cast<T*>(m->core);
+  d.Gmask = m->core_mask;
+  return d;
+}
+
+// Per-mode CSR view handed to kernels.
+template <typename T>
+struct DevMode {
+  const int64_t* nzptr;
+  const int32_t* nzrow;
+  const int32_t* nnzrows;
+  const int32_t* oidx;  // [(N-1)][nnz]
+  const T* val;
+  const int32_t* perm;
+  int64_t nnz;
+};
+
+template <typename T>
+inline DevMode<T> dev_mode(const vest_index* ix, int n) {
+  DevMode<T> d;
+  const ModeIndex& mi = ix->mode[n];
+  d.nzptr = mi.nzptr;
+  d.nzrow = mi.nzrow;
+  d.nnzrows = mi.nnzrows;
+  d.oidx = mi.oidx;
+  d.val = static_cast<const T*>(mi.val);
+  d.perm = mi.perm;
+  d.nnz = ix->nnz;
+  return d;
+}
+
+// ------------------------------------------------------------------ scratch layout
+// Scratch is carved into fixed regions; every compute call validates the size.
+struct ScratchPlan {
+  size_t total;
+  size_t off_status, off_gperm, off_spill, off_spanning, off_resid, off_resid_coo, off_part, off_small;
+  size_t off_prune_keys, off_prune_vals, off_prune_tmp;
+  size_t gperm_bytes, spill_bytes, part_bytes;
+  int task;        // alpha per task in the factor sweep
+  int64_t ntasks;  // factor-sweep tasks per mode
+};
+
+ScratchPlan plan_scratch(const vest_index* ix, const vest_model* m);
+
+// ------------------------------------------------------------------ helpers
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+int num_sms();
+
+// Generic device scans (exclusive) used by the index build and the prune.
+vest_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, cudaStream_t s);
+vest_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s);
+size_t scan_tmp_elems(int64_t n);
+
+// Stable LSD radix sort of (key, value) pairs; `bits` low bits of the key are significant.
+template <typename K>
+vest_status radix_sort_pairs(K* keys, int32_t* vals, K* keys_alt, int32_t* vals_alt, int64_t n, int bits,
+                             int32_t* hist, int32_t* scan_tmp, bool* result_in_alt, cudaStream_t s);
+size_t radix_hist_elems(int64_t n);
+
+// Operations implemented in their own translation units.
+template <typename T>
+vest_status sweep_factors_mode(const vest_index* ix, const vest_model* m, int reg, double lambda, int mode,
+                               char* scratch, const ScratchPlan& plan, cudaStream_t s);
+template <typename T>
+vest_status responsibility_factors(const vest_index* ix, const vest_model* m, const double* stats,
+                                   double* const* delta_factor, double* const* resp_factor, char* scratch,
+                                   const ScratchPlan& plan, cudaStream_t s);
+template <typename T>
+vest_status loss_impl(const vest_index* ix, const vest_model* m, int reg, double lambda, double* out,
+                      T* resid_csr0, T* resid_coo, char* scratch, const ScratchPlan& plan, cudaStream_t s);
+template <typename T>
+vest_status sweep_core_impl(const vest_index* ix, const vest_model* m, int reg, double lambda, char* scratch,
+                            const ScratchPlan& plan, cudaStream_t s);
+template <typename T>
+vest_status core_responsibility(const vest_index* ix, const vest_model* m, const T* resid_csr0,
+                                const double* stats, double* delta_core, double* resp_core, char* scratch,
+                                const ScratchPlan& plan, cudaStream_t s);
+template <typename T>
+vest_status prune_impl(const vest_model* m, double* const* delta_factor, const double* delta_core, double pr,
+                       int count_mode, int threshold_mode, double tau, int64_t* n_pruned, char* scratch,
+                       const ScratchPlan& plan, cudaStream_t s);
+template <typename T>
+vest_status normalize_impl(const vest_model* m, char* scratch, cudaStream_t s);
+template <typename T>
+vest_status count_zeros_impl(const vest_model* m, int64_t* out, char* scratch, cudaStream_t s);
+template <typename T>
+vest_status reconstruct_impl(const vest_model* m, const int32_t* q_idx, int64_t count, T* out, cudaStream_t s);
+
+vest_status build_index_impl(const vest_tensor* t, void* ws, size_t ws_bytes, vest_index* ix, cudaStream_t s);
+size_t index_workspace_bytes(const vest_tensor* t);
+
+// ------------------------------------------------------------------ device helpers
+// Largest k in [0, n] with a[k] <= x (a sorted ascending, a[0] <= x).
+template <typename I>
+__device__ __forceinline__ int64_t upper_bound_m1(const I* a, int64_t n, int64_t x) {
+  int64_t lo = 0, hi = n;  // invariant: a[lo] <= x, answer in [lo, hi]
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) >> 1;
+    if ((int64_t)a[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace vest
