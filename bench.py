@@ -295,7 +295,7 @@ def main():
         tt = torch.tensor([e2e_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
-    e2e_value = world * units_per_step * args.e2e_steps / (e2e_ms / 1e3)
+    e2e_value = world * units_per_step * args.e2e_steps / (e2e_ms / 1e3) if args.e2e_steps > 0 else None
 
     if rank != 0:
         if world > 1:
