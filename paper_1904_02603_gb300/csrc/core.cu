@@ -101,6 +101,31 @@ __device__ __forceinline__ void entry_kl(int e, int b, int& k, int& l) {
   l = kk + u;
 }
 
+// Terms of the per-piece sums: packed upper Q = sum w w^T, then h = sum r w.
+template <typename T>
+struct CoreTerm {
+  const T* sW;
+  const T* sR;
+  int m;
+  struct Prep {
+    int kind, a, b;
+  };
+  __device__ Prep prep(int p) const {
+    const int nq = m * (m + 1) / 2;
+    if (p >= nq) return Prep{1, p - nq, 0};
+    int u = p, q = 0;
+    while (u >= m - q) {
+      u -= m - q;
+      ++q;
+    }
+    return Prep{0, q, q + u};
+  }
+  __device__ T eval(const Prep& pr, int x) const {
+    const T* w = sW + x * m;
+    return pr.kind == 0 ? w[pr.a] * w[pr.b] : sR[x] * w[pr.a];
+  }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kCoreTask) core_pass_kernel(DevModel<T> M, DevMode<T> csr, const T* r_in,
                                                               T* r_out, CoreArgs a) {
@@ -115,7 +140,9 @@ __global__ void __launch_bounds__(kCoreTask) core_pass_kernel(DevModel<T> M, Dev
   T* sU = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * max(mp, 1) * sizeof(T);
   T* sW = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * m * sizeof(T);
   T* sR = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * sizeof(T);
-  T* sQ = reinterpret_cast<T*>(smem_raw + off);
+  T* sQ = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * QP * sizeof(T);
+  T* sPart = reinterpret_cast<T*>(smem_raw + off);
+  __shared__ PieceScratch pscr;
 
   if (a.has_prev)
     for (int i = threadIdx.x; i < a.prev.b; i += blockDim.x) sdp[i] = a.dprev[i];
@@ -185,26 +212,10 @@ __global__ void __launch_bounds__(kCoreTask) core_pass_kernel(DevModel<T> M, Dev
     }
     __syncthreads();
     // phase 2: per row piece Q (packed upper) and h
-    for (int k = warp; k < nrows; k += nwarps) {
-      const int s = (int)(max(sptr[k], t0) - t0), e = (int)(min(sptr[k + 1], t1) - t0);
-      for (int pi = lane; pi < QP; pi += 32) {
-        T v = T(0);
-        if (pi < m * (m + 1) / 2) {
-          int u = pi, q = 0;
-          while (u >= m - q) {
-            u -= m - q;
-            ++q;
-          }
-          const int q2 = q + u;
-          for (int x = s; x < e; ++x) v += sW[x * m + q] * sW[x * m + q2];
-        } else {
-          const int q = pi - m * (m + 1) / 2;
-          for (int x = s; x < e; ++x) v += sR[x] * sW[x * m + q];
-        }
-        sQ[k * QP + pi] = v;
-      }
+    {
+      CoreTerm<T> f{sW, sR, m};
+      piece_sums<T>(sptr, nrows, t0, t1, QP, sQ, sPart, &pscr, f);
     }
-    __syncthreads();
     // phase 3: M += (a0 a0^T) (x) Q, g += a0 (x) h, over the pieces
     for (int k = 0; k < nrows; ++k) {
       const T* a0 = sA0 + k * J0;
@@ -326,6 +337,7 @@ static size_t pass_smem(int J0, int m, int mp) {
   off += (size_t)kCoreTask * m * sizeof(T);
   off += (size_t)kCoreTask * sizeof(T);
   off += (size_t)kCoreTask * QP * sizeof(T);
+  off += (size_t)kMaxLongPieces * QP * sizeof(T);
   return off;
 }
 

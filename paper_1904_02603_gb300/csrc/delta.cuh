@@ -212,6 +212,98 @@ __device__ __forceinline__ int load_task_rows(const int64_t* __restrict__ nzptr,
   return nrows;
 }
 
+// ---------------------------------------------------------------- per-piece sums
+// sums[k * P + p] = sum over the entries q of row piece k (task-local positions
+// [max(sptr[k], t0), min(sptr[k+1], t1)) - t0) of f.eval(f.prep(p), q).
+// Pieces of at most kPieceChunk entries: one warp per piece, lanes over p.
+// Longer pieces (at most TASK / kPieceChunk of them): cut into kPieceChunk-entry
+// chunks spread over every thread, partials combined in chunk order.  Each
+// chain keeps two accumulators (even / odd entries).  Fixed order throughout.
+constexpr int kPieceChunk = 32;
+constexpr int kMaxLongPieces = 16;
+
+struct PieceScratch {
+  int nlong;
+  int total;                       // items of long pieces
+  int k[kMaxLongPieces];           // long piece ids
+  int q[kMaxLongPieces];           // chunks per long piece
+  int item0[kMaxLongPieces + 1];   // first item of each long piece
+};
+
+template <typename S, typename F>
+__device__ __forceinline__ S chain_sum(const F& f, const typename F::Prep& pr, int s, int e) {
+  S a0 = S(0), a1 = S(0);
+  int q = s;
+  for (; q + 1 < e; q += 2) {
+    a0 += f.eval(pr, q);
+    a1 += f.eval(pr, q + 1);
+  }
+  if (q < e) a0 += f.eval(pr, q);
+  return a0 + a1;
+}
+
+template <typename S, typename F>
+__device__ void piece_sums(const int64_t* sptr, int nrows, int64_t t0, int64_t t1, int P, S* sums, S* part,
+                           PieceScratch* ps, const F& f) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // short pieces
+  for (int k = warp; k < nrows; k += nwarps) {
+    const int s = (int)(max(sptr[k], t0) - t0), e = (int)(min(sptr[k + 1], t1) - t0);
+    if (e - s > kPieceChunk) continue;
+    for (int p = lane; p < P; p += 32) sums[k * P + p] = chain_sum<S>(f, f.prep(p), s, e);
+  }
+  // collect long pieces (warp 0)
+  if (warp == 0) {
+    int n = 0;
+    for (int k0 = 0; k0 < nrows; k0 += 32) {
+      const int k = k0 + lane;
+      bool lg = false;
+      if (k < nrows) lg = (min(sptr[k + 1], t1) - max(sptr[k], t0)) > kPieceChunk;
+      const unsigned b = __ballot_sync(0xffffffffu, lg);
+      if (lg) {
+        const int slot = n + __popc(b & ((1u << lane) - 1u));
+        if (slot < kMaxLongPieces) ps->k[slot] = k;
+      }
+      n += __popc(b);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      ps->nlong = min(n, kMaxLongPieces);
+      int it = 0;
+      for (int i = 0; i < ps->nlong; ++i) {
+        const int k = ps->k[i];
+        const int len = (int)(min(sptr[k + 1], t1) - max(sptr[k], t0));
+        ps->q[i] = (len + kPieceChunk - 1) / kPieceChunk;
+        ps->item0[i] = it;
+        it += ps->q[i] * P;
+      }
+      ps->item0[ps->nlong] = it;
+      ps->total = it;
+    }
+  }
+  __syncthreads();
+  const int nlong = ps->nlong, total = ps->total;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    int j = 0;
+    while (i >= ps->item0[j + 1]) ++j;
+    const int k = ps->k[j], r = i - ps->item0[j];
+    const int q = r / P, p = r % P;
+    const int s0 = (int)(max(sptr[k], t0) - t0), e0 = (int)(min(sptr[k + 1], t1) - t0);
+    const int s = s0 + q * kPieceChunk, e = min(e0, s + kPieceChunk);
+    part[i] = chain_sum<S>(f, f.prep(p), s, e);
+  }
+  __syncthreads();
+  for (int j = 0; j < nlong; ++j) {
+    const int k = ps->k[j], nq = ps->q[j], base = ps->item0[j];
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+      S a = S(0);
+      for (int q = 0; q < nq; ++q) a += part[base + q * P + p];
+      sums[k * P + p] = a;
+    }
+  }
+  __syncthreads();
+}
+
 // local row of position p: largest q < nrows with sptr[q] <= p
 __device__ __forceinline__ int local_row(const int64_t* sptr, int nrows, int64_t p) {
   int lo = 0, hi = nrows - 1;

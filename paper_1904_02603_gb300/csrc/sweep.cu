@@ -4,10 +4,11 @@
 // Work is cut into tasks of TASK consecutive CSR positions (nnz-balanced, so
 // heavy Zipf rows and one-entry rows cost the same per entry):
 //   phase 1  one thread per entry: delta_alpha (Eq. 11) into shared memory;
-//   phase 2  one warp per row piece, lanes over outputs: the row sums
-//            c_j = sum X delta_j and V_jt = sum delta_j delta_t (Eq. 10) for the
-//            update, or sum r delta_j and sum delta_j^2 for the responsibility,
-//            summed over the piece in CSR order (accumulator: T);
+//   phase 2  the row sums c_j = sum X delta_j and V_jt = sum delta_j delta_t
+//            (Eq. 10) for the update, or sum r delta_j and sum delta_j^2 for the
+//            responsibility, per row piece (accumulator: T): short pieces one
+//            warp each, long pieces cut into 32-entry chunks over all warps and
+//            combined in chunk order;
 //   phase 3  one thread per row: rows that lie inside the task are finished
 //            at once (sequential CD over j, FP64); a row cut by a task edge
 //            writes its piece to a spill slot, and the task where the row
@@ -91,6 +92,35 @@ __device__ void finish_row(const DevModel<T>& M, int n, int64_t row, const S* su
   }
 }
 
+// Terms of the row sums: update mode c_j = sum X delta_j (p < Jn), then the packed
+// upper Gram delta_j delta_t; responsibility mode sum r delta_j, then sum delta_j^2.
+template <typename T, typename S, int MODE>
+struct SweepTerm {
+  const T* sD;
+  const T* sX;
+  int JNS, Jn;
+  struct Prep {
+    int kind, j, t;
+  };
+  __device__ Prep prep(int p) const {
+    if (p < Jn) return Prep{0, p, 0};
+    if constexpr (MODE == kModeUpdate) {
+      int u = p - Jn, j = 0;
+      while (u >= Jn - j) {
+        u -= Jn - j;
+        ++j;
+      }
+      return Prep{1, j, j + u};
+    } else {
+      return Prep{1, p - Jn, p - Jn};
+    }
+  }
+  __device__ S eval(const Prep& pr, int q) const {
+    const T* d = sD + q * JNS;
+    return pr.kind == 0 ? (S)sX[q] * (S)d[pr.j] : (S)d[pr.j] * (S)d[pr.t];
+  }
+};
+
 template <typename T, int JN, int NSLOW, int MODE>
 __global__ void __launch_bounds__(256) sweep_task_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ gcore,
                                                          SweepArgs a) {
@@ -113,6 +143,9 @@ __global__ void __launch_bounds__(256) sweep_task_kernel(DevModel<T> M, DevMode<
   off += (size_t)TASK * sizeof(T);
   off = (off + 15) & ~(size_t)15;
   S* sAcc = reinterpret_cast<S*>(smem_raw + off);
+  off += (size_t)TASK * P * sizeof(S);
+  S* sPart = reinterpret_cast<S*>(smem_raw + off);
+  __shared__ PieceScratch pscr;
 
   const T* g = gcore;
   if (a.use_smem_core) {
@@ -121,7 +154,6 @@ __global__ void __launch_bounds__(256) sweep_task_kernel(DevModel<T> M, DevMode<
   }
   const int R = *csr.nnzrows;
   const int64_t nnz = csr.nnz;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int n = r.n;
   const int Jn = r.Jn;
   __syncthreads();
@@ -148,28 +180,10 @@ __global__ void __launch_bounds__(256) sweep_task_kernel(DevModel<T> M, DevMode<
     __syncthreads();
 
     // phase 2: per-row sums over the task's piece of the row
-    for (int k = warp; k < nrows; k += nwarps) {
-      const int s = (int)(max(sptr[k], t0) - t0), e = (int)(min(sptr[k + 1], t1) - t0);
-      for (int pi = lane; pi < P; pi += 32) {
-        S acc = S(0);
-        if (pi < Jn) {
-          for (int q = s; q < e; ++q) acc += (S)sX[q] * (S)sD[q * JNS + pi];
-        } else if constexpr (MODE == kModeUpdate) {
-          int u = pi - Jn, j = 0;
-          while (u >= Jn - j) {
-            u -= Jn - j;
-            ++j;
-          }
-          const int t = j + u;
-          for (int q = s; q < e; ++q) acc += (S)sD[q * JNS + j] * (S)sD[q * JNS + t];
-        } else {
-          const int j = pi - Jn;
-          for (int q = s; q < e; ++q) acc += (S)sD[q * JNS + j] * (S)sD[q * JNS + j];
-        }
-        sAcc[k * P + pi] = acc;
-      }
+    {
+      SweepTerm<T, S, MODE> f{sD, sX, JNS, Jn};
+      piece_sums<S>(sptr, nrows, t0, t1, P, sAcc, sPart, &pscr, f);
     }
-    __syncthreads();
 
     // phase 3: finish whole rows, spill cut ones
     for (int k = threadIdx.x; k < nrows; k += blockDim.x) {
@@ -262,6 +276,7 @@ static size_t task_smem(int task, int JN, int P, size_t core_bytes) {
   off += (size_t)task * sizeof(T);
   off = (off + 15) & ~(size_t)15;
   off += (size_t)task * P * sizeof(typename AccOf<T>::type);
+  off += (size_t)kMaxLongPieces * P * sizeof(typename AccOf<T>::type);
   return off;
 }
 
