@@ -225,6 +225,27 @@ size_t vest_autosearch_scratch_bytes(const vest_index* ix, const vest_model* m);
 vest_status vest_autosearch(const vest_index* ix, vest_model* m, const vest_params* p, vest_report* report,
                             void* scratch, size_t scratch_bytes, void* stream);
 
+/* ---- vest_loss without a scratch buffer.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they
+ * need the loss, such as a host runtime that owns the device heap and forbids
+ * other allocations, or a service whose memory budget is fixed at start-up.
+ * It computes exactly what vest_loss() computes (out: device double[5];
+ * resid: optional device [nnz] in COO order) and allocates nothing: its
+ * scratch is a fixed 1 MiB array inside libvest, present on every device that
+ * loads the library until the process exits.
+ *   - Limit: the permuted mode-0 core (prod_n J_n rounded up to the rank bucket,
+ *     in the model dtype) plus about 12 KB of partial sums must fit in 1 MiB;
+ *     larger models get VEST_ERR_WORKSPACE and should use vest_loss().
+ *   - The first call on a device looks up the array's device address (one
+ *     cudaGetSymbolAddress with that device current) and caches it; make that
+ *     first call before any stream capture.
+ *   - Every call on a device shares the one array and overwrites what the
+ *     previous call left there (nothing in it needs to start at zero: each
+ *     call writes every value it reads).  Calls that overlap on the GPU race
+ *     on it: serialise them, e.g. on one stream. */
+vest_status vest_loss_noalloc(const vest_index* ix, const vest_model* m, int32_t reg, double lambda, double* out,
+                              void* resid, void* stream);
+
 /* Completion queries: B(alpha) (Eq. 7) for m query positions q_idx (device
  * int32 [order][m]) into out (device, model dtype, [m]). */
 vest_status vest_reconstruct(const vest_model* m, const int32_t* q_idx, int64_t count, void* out,

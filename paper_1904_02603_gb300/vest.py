@@ -84,6 +84,7 @@ _SIGS = {
     "vest_autosearch": (C.c_int, [_P, C.POINTER(vest_model), C.POINTER(vest_params), C.POINTER(vest_report), _P,
                                   C.c_size_t, _P]),
     "vest_reconstruct": (C.c_int, [C.POINTER(vest_model), _P, C.c_int64, _P, _P]),
+    "vest_loss_noalloc": (C.c_int, [_P, C.POINTER(vest_model), C.c_int32, C.c_double, _P, _P, _P]),
 }
 
 _lib = None
@@ -315,6 +316,14 @@ def vest_loss(ix: Index, m: Model, reg: int, lam: float, scratch: torch.Tensor, 
         out = torch.empty(5, dtype=torch.float64, device="cuda")
     _call("vest_loss", ix.handle, C.byref(m.cstruct()), reg, lam, _dptr(out), _dptr(resid), _dptr(scratch),
           scratch.numel(), _stream(stream))
+    return out
+
+
+def vest_loss_noalloc(ix: Index, m: Model, reg: int, lam: float, out=None, resid=None, stream=None):
+    """vest_loss without a scratch buffer: the library's fixed 1 MiB device array is used instead."""
+    if out is None:
+        out = torch.empty(5, dtype=torch.float64, device="cuda")
+    _call("vest_loss_noalloc", ix.handle, C.byref(m.cstruct()), reg, lam, _dptr(out), _dptr(resid), _stream(stream))
     return out
 
 
