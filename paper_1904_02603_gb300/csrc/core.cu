@@ -28,7 +28,7 @@ namespace vest {
 constexpr int kCoreTask = 256;
 constexpr int kCoreMaxB = 128;
 constexpr int kCoreMaxM = 10;
-constexpr int kCoreEPT = 36;           // accumulator entries per thread (>= (128*129/2 + 128)/256)
+constexpr int kCoreEPT = 24;           // accumulator entries per thread (nz <= 5408 for b <= 128, m <= 10)
 constexpr int kCorePassCtas = 296;     // fixed: reduction order does not depend on the device
 
 struct CoreBlock {
@@ -43,7 +43,8 @@ struct CoreArgs {
   int64_t ntasks;
   CoreBlock cur, prev;
   int has_prev;
-  int nent;               // b(b+1)/2 + b accumulator entries
+  int nent;               // b(b+1)/2 + b entries of the packed Gram and g
+  int nz;                 // Kronecker-form accumulator entries
   const double* dprev;    // Delta of the previous block [b_prev]
   double* part;           // [ctas][nent]
 };
@@ -62,26 +63,23 @@ __device__ __forceinline__ T suffix_weight(const DevModel<T>& M, const int32_t* 
   return c;
 }
 
+// Running sums across tasks: Kahan-compensated for FP32, plain for FP64.
 template <typename T>
 struct CoreAcc;
 template <>
 struct CoreAcc<float> {
-  float s, c;
-  __device__ void zero() { s = 0.f; c = 0.f; }
-  __device__ void add(float v) {  // Kahan
+  static __device__ void add(float& s, float& c, float v) {
     const float y = v - c;
     const float t = s + y;
     c = (t - s) - y;
     s = t;
   }
-  __device__ double value() const { return (double)s - (double)c; }
+  static __device__ double value(float s, float c) { return (double)s - (double)c; }
 };
 template <>
 struct CoreAcc<double> {
-  double s;
-  __device__ void zero() { s = 0.0; }
-  __device__ void add(double v) { s += v; }
-  __device__ double value() const { return s; }
+  static __device__ void add(double& s, double&, double v) { s += v; }
+  static __device__ double value(double s, double) { return s; }
 };
 
 // entry e of the packed accumulator -> (k, l): e < b(b+1)/2 packed upper M (k <= l), else g_k
@@ -107,22 +105,15 @@ struct CoreTerm {
   const T* sW;
   const T* sR;
   int m;
-  struct Prep {
-    int kind, a, b;
-  };
-  __device__ Prep prep(int p) const {
+  __device__ TermPtrs<T> prep(int p) const {
     const int nq = m * (m + 1) / 2;
-    if (p >= nq) return Prep{1, p - nq, 0};
+    if (p >= nq) return TermPtrs<T>{sR, sW + (p - nq), 1, m};
     int u = p, q = 0;
     while (u >= m - q) {
       u -= m - q;
       ++q;
     }
-    return Prep{0, q, q + u};
-  }
-  __device__ T eval(const Prep& pr, int x) const {
-    const T* w = sW + x * m;
-    return pr.kind == 0 ? w[pr.a] * w[pr.b] : sR[x] * w[pr.a];
+    return TermPtrs<T>{sW + q, sW + q + u, m, m};
   }
 };
 
@@ -141,34 +132,42 @@ __global__ void __launch_bounds__(kCoreTask) core_pass_kernel(DevModel<T> M, Dev
   T* sW = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * m * sizeof(T);
   T* sR = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * sizeof(T);
   T* sQ = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * QP * sizeof(T);
-  T* sPart = reinterpret_cast<T*>(smem_raw + off);
+  T* sPart = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kMaxLongPieces * QP * sizeof(T);
+  T* sSum = reinterpret_cast<T*>(smem_raw + off); off += (size_t)a.nz * sizeof(T);
+  T* sComp = reinterpret_cast<T*>(smem_raw + off);
   __shared__ PieceScratch pscr;
 
   if (a.has_prev)
     for (int i = threadIdx.x; i < a.prev.b; i += blockDim.x) sdp[i] = a.dprev[i];
 
-  // accumulator entries owned by this thread, each coded as
-  // a0 index 1 (8 bits) | a0 index 2 (8 bits, 255 = g entry) | offset into Q (16 bits)
-  CoreAcc<T> acc[kCoreEPT];
+  // Block Gram in Kronecker form: Z[xi][yi] = sum over row pieces of
+  // X[xi] * Y[yi], X = packed upper a0 a0^T (nX = J0(J0+1)/2 values), Y = packed
+  // upper Q (nY = m(m+1)/2), followed by the J0*m products a0[j0] * h[q] of g.
+  // Each thread owns entries threadIdx.x + i * blockDim.x, coded as
+  // a0 index 1 (8 bits) | a0 index 2 (8 bits, 255 = g entry) | offset into Q/h (16 bits).
+  T tacc[kCoreEPT];
   uint32_t code[kCoreEPT];
   int nown = 0;
+  const int nY = m * (m + 1) / 2, nX = J0 * (J0 + 1) / 2;
 #pragma unroll
   for (int i = 0; i < kCoreEPT; ++i) {
-    acc[i].zero();
     code[i] = 0xFFFFFFFFu;
     const int e = threadIdx.x + i * blockDim.x;
-    if (e < a.nent) {
-      int kk, ll;
-      entry_kl(e, b, kk, ll);
-      const int j0 = kk % J0, q = kk / J0;
-      if (ll >= 0) {
-        const int j0b = ll % J0, qb = ll / J0;
-        const int lo = min(q, qb), hi = max(q, qb);
-        code[i] = (uint32_t)j0 | ((uint32_t)j0b << 8) | ((uint32_t)(lo * m - (lo * (lo - 1)) / 2 + (hi - lo)) << 16);
+    if (e < a.nz) {
+      if (e < nX * nY) {
+        int u = e / nY, ja = 0;
+        while (u >= J0 - ja) {
+          u -= J0 - ja;
+          ++ja;
+        }
+        code[i] = (uint32_t)ja | ((uint32_t)(ja + u) << 8) | ((uint32_t)(e % nY) << 16);
       } else {
-        code[i] = (uint32_t)j0 | (255u << 8) | ((uint32_t)(m * (m + 1) / 2 + q) << 16);
+        const int g = e - nX * nY;
+        code[i] = (uint32_t)(g % J0) | (255u << 8) | ((uint32_t)(nY + g / J0) << 16);
       }
       nown = i + 1;
+      sSum[e] = T(0);
+      sComp[e] = T(0);
     }
   }
   const int R = *csr.nnzrows;
@@ -179,7 +178,7 @@ __global__ void __launch_bounds__(kCoreTask) core_pass_kernel(DevModel<T> M, Dev
     const int64_t t0 = task * kCoreTask, t1 = min(t0 + (int64_t)kCoreTask, a.nnz);
     const int cnt = (int)(t1 - t0);
     int64_t k0;
-    const int nrows = load_task_rows(csr.nzptr, R, t0, t1, sptr, &k0);
+    const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, sptr, &k0);
     // row data: a0 row and u(q) = sum_j0 Delta_prev(j0, q) a0[j0]
     for (int k = warp; k < nrows; k += nwarps) {
       const int64_t row = csr.nzrow[k0 + k];
@@ -216,7 +215,10 @@ __global__ void __launch_bounds__(kCoreTask) core_pass_kernel(DevModel<T> M, Dev
       CoreTerm<T> f{sW, sR, m};
       piece_sums<T>(sptr, nrows, t0, t1, QP, sQ, sPart, &pscr, f);
     }
-    // phase 3: M += (a0 a0^T) (x) Q, g += a0 (x) h, over the pieces
+    // phase 3: Z += X (x) Y and g += a0 (x) h over the task's pieces (storage type),
+    // then into the block's running sums (Kahan for FP32)
+#pragma unroll
+    for (int i = 0; i < kCoreEPT; ++i) tacc[i] = T(0);
     for (int k = 0; k < nrows; ++k) {
       const T* a0 = sA0 + k * J0;
       const T* Q = sQ + k * QP;
@@ -225,25 +227,52 @@ __global__ void __launch_bounds__(kCoreTask) core_pass_kernel(DevModel<T> M, Dev
         if (i >= nown) continue;
         const uint32_t c = code[i];
         const int ia = (int)(c & 255u), ib = (int)((c >> 8) & 255u), iq = (int)(c >> 16);
-        const T v = ib == 255 ? a0[ia] * Q[iq] : a0[ia] * a0[ib] * Q[iq];
-        acc[i].add(v);
+        const T xa = ib == 255 ? a0[ia] : a0[ia] * a0[ib];
+        tacc[i] += xa * Q[iq];
       }
     }
+#pragma unroll
+    for (int i = 0; i < kCoreEPT; ++i)
+      if (i < nown) {
+        const int e = threadIdx.x + i * blockDim.x;
+        CoreAcc<T>::add(sSum[e], sComp[e], tacc[i]);
+      }
     __syncthreads();
   }
 #pragma unroll
   for (int i = 0; i < kCoreEPT; ++i)
-    if (i < nown) a.part[(size_t)blockIdx.x * a.nent + threadIdx.x + i * blockDim.x] = acc[i].value();
+    if (i < nown) {
+      const int e = threadIdx.x + i * blockDim.x;
+      a.part[(size_t)blockIdx.x * a.nz + e] = CoreAcc<T>::value(sSum[e], sComp[e]);
+    }
 }
 
-// Fixed-order FP64 sum of the per-block partials.
-__global__ void core_merge_kernel(const double* __restrict__ part, int nctas, int nent, double* __restrict__ tot) {
+__device__ __forceinline__ int sym_index(int x, int y, int n) {
+  const int lo = min(x, y), hi = max(x, y);
+  return lo * n - (lo * (lo - 1)) / 2 + (hi - lo);
+}
+
+// Fixed-order FP64 sum of the per-block partials, expanded from the Kronecker
+// form into the packed block Gram M (k <= l) followed by g.
+__global__ void core_merge_kernel(const double* __restrict__ part, int nctas, int nz, int nent, int b, int J0, int m,
+                                  double* __restrict__ tot) {
+  const int nm = b * (b + 1) / 2, nY = m * (m + 1) / 2, nX = J0 * (J0 + 1) / 2;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nent; e += gridDim.x * blockDim.x) {
+    int z;
+    if (e < nm) {
+      int k, l;
+      entry_kl(e, b, k, l);
+      z = sym_index(k % J0, l % J0, J0) * nY + sym_index(k / J0, l / J0, m);
+    } else {
+      const int k = e - nm;
+      z = nX * nY + (k % J0) + J0 * (k / J0);
+    }
     double s = 0.0;
-    for (int c = 0; c < nctas; ++c) s += part[(size_t)c * nent + e];
+    for (int c = 0; c < nctas; ++c) s += part[(size_t)c * nz + z];
     tot[e] = s;
   }
 }
+
 
 // Exact sequential updates of one block (Eq. 12 / Eq. 14), one thread block.
 template <typename T>
@@ -324,12 +353,12 @@ size_t core_part_bytes(const vest_model* m) {
   int mm;
   int64_t S;
   plan_blocks(m->ranks, m->order, &mm, &S);
-  const int b = m->ranks[0] * mm;
-  return (size_t)kCorePassCtas * (size_t)(b * (b + 1) / 2 + b) * 8;
+  const int J0 = m->ranks[0];
+  return (size_t)kCorePassCtas * (size_t)((J0 * (J0 + 1) / 2) * (mm * (mm + 1) / 2) + J0 * mm) * 8;
 }
 
 template <typename T>
-static size_t pass_smem(int J0, int m, int mp) {
+static size_t pass_smem(int J0, int m, int mp, int nz) {
   const int QP = m * (m + 1) / 2 + m;
   size_t off = (size_t)(kCoreTask + 2) * 8 + (size_t)kCoreMaxB * 8;
   off += (size_t)kCoreTask * J0 * sizeof(T);
@@ -338,6 +367,7 @@ static size_t pass_smem(int J0, int m, int mp) {
   off += (size_t)kCoreTask * sizeof(T);
   off += (size_t)kCoreTask * QP * sizeof(T);
   off += (size_t)kMaxLongPieces * QP * sizeof(T);
+  off += 2 * (size_t)nz * sizeof(T);
   return off;
 }
 
@@ -371,16 +401,19 @@ static vest_status core_blocks(const vest_index* ix, const vest_model* mdl, int 
       blk.b = a.J0 * blk.m;
       a.cur = blk;
       a.nent = blk.b * (blk.b + 1) / 2 + blk.b;
-      if ((size_t)nctas * a.nent * 8 > plan.part_bytes) return fail(VEST_ERR_WORKSPACE, "core partial region too small");
+      a.nz = (a.J0 * (a.J0 + 1) / 2) * (blk.m * (blk.m + 1) / 2) + a.J0 * blk.m;
+      if ((size_t)nctas * a.nz * 8 > plan.part_bytes) return fail(VEST_ERR_WORKSPACE, "core partial region too small");
+      if (a.nz > kCoreEPT * kCoreTask) return fail(VEST_ERR_UNSUPPORTED, "core block too large");
       a.has_prev = (solve && iblk > 0) ? 1 : 0;
       a.dprev = dbuf[(iblk + 1) & 1];
       if (ix->nnz > 0) {
-        const size_t smem = pass_smem<T>(a.J0, blk.m, a.has_prev ? a.prev.m : 0);
+        const size_t smem = pass_smem<T>(a.J0, blk.m, a.has_prev ? a.prev.m : 0, a.nz);
         auto kern = core_pass_kernel<T>;
         VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<nctas, kCoreTask, smem, s>>>(M, csr, r0, r0, a);
         VEST_LAUNCH("core_pass_kernel");
-        core_merge_kernel<<<(unsigned)ceil_div(a.nent, 256), 256, 0, s>>>(a.part, nctas, a.nent, tot);
+        core_merge_kernel<<<(unsigned)ceil_div(a.nent, 256), 256, 0, s>>>(a.part, nctas, a.nz, a.nent, blk.b, a.J0,
+                                                                          blk.m, tot);
         VEST_LAUNCH("core_merge_kernel");
       } else {
         VEST_CUDA(cudaMemsetAsync(tot, 0, (size_t)a.nent * 8, s));

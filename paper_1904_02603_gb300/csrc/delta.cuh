@@ -178,13 +178,161 @@ __device__ __forceinline__ void compute_delta(T (&d)[JN], const T* __restrict__ 
   }
 }
 
+// ---------------------------------------------------------------- delta for E entries at once
+// The core fibre of each (o, j_f) is read from shared memory once and feeds all
+// E entries of the thread.  JF > 0: the rank of mode f is JF at compile time and
+// the E rows of mode f sit in registers.
+template <typename T, int JN>
+__device__ __forceinline__ void load_fibre(T (&v)[JN], const T* __restrict__ g) {
+  if constexpr (sizeof(T) == 4 && JN % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < JN; j += 4) {
+      const float4 x = *reinterpret_cast<const float4*>(g + j);
+      v[j] = x.x;
+      v[j + 1] = x.y;
+      v[j + 2] = x.z;
+      v[j + 3] = x.w;
+    }
+  } else if constexpr (sizeof(T) == 4 && JN % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < JN; j += 2) {
+      const float2 x = *reinterpret_cast<const float2*>(g + j);
+      v[j] = x.x;
+      v[j + 1] = x.y;
+    }
+  } else if constexpr (sizeof(T) == 8 && JN % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < JN; j += 2) {
+      const double2 x = *reinterpret_cast<const double2*>(g + j);
+      v[j] = x.x;
+      v[j + 1] = x.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < JN; ++j) v[j] = g[j];
+  }
+}
+
+template <typename T, int JN, int JF, int E>
+__device__ __forceinline__ void delta_slice(T (&d)[E][JN], const T (&w)[E], const T* __restrict__ go, int Jf,
+                                            const T* const (&rowf)[E], const T (&rf)[E][JF > 0 ? JF : 1]) {
+  if constexpr (JF > 0) {
+#pragma unroll
+    for (int cf = 0; cf < JF; ++cf) {
+      T gv[JN];
+      load_fibre<T, JN>(gv, go + cf * JN);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const T wf = w[e] * rf[e][cf];
+#pragma unroll
+        for (int j = 0; j < JN; ++j) d[e][j] = fma(wf, gv[j], d[e][j]);
+      }
+    }
+  } else {
+    for (int cf = 0; cf < Jf; ++cf) {
+      T gv[JN];
+      load_fibre<T, JN>(gv, go + cf * JN);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const T wf = w[e] * __ldg(rowf[e] + cf);
+#pragma unroll
+        for (int j = 0; j < JN; ++j) d[e][j] = fma(wf, gv[j], d[e][j]);
+      }
+    }
+  }
+}
+
+template <typename T, int JN, int JF, int NSLOW, int E>
+__device__ __forceinline__ void compute_delta_multi(T (&d)[E][JN], const T* __restrict__ g,
+                                                    const uint8_t* __restrict__ onz, int64_t n_outer, int Jf,
+                                                    const T* const (&rowf)[E], const SlowRows (&sr)[E], int nslow) {
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+#pragma unroll
+    for (int j = 0; j < JN; ++j) d[e][j] = T(0);
+  T rf[E][JF > 0 ? JF : 1];
+  if constexpr (JF > 0) {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int cf = 0; cf < JF; ++cf) rf[e][cf] = __ldg(rowf[e] + cf);
+  }
+  const int64_t slice = (int64_t)Jf * JN;
+  T w[E];
+  if constexpr (NSLOW == 0) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) w[e] = T(1);
+    delta_slice<T, JN, JF, E>(d, w, g, Jf, rowf, rf);
+  } else if constexpr (NSLOW == 1) {
+    for (int o = 0; o < (int)n_outer; ++o) {
+      if (!onz[o]) continue;
+      bool any = false;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        w[e] = __ldg(static_cast<const T*>(sr[e].row[0]) + o);
+        any |= (w[e] != T(0));
+      }
+      if (!any) continue;
+      delta_slice<T, JN, JF, E>(d, w, g + o * slice, Jf, rowf, rf);
+    }
+  } else if constexpr (NSLOW == 2) {
+    const int J0 = sr[0].J[0], J1 = sr[0].J[1];
+    for (int d1 = 0; d1 < J1; ++d1) {
+      T w1[E];
+      bool any1 = false;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        w1[e] = __ldg(static_cast<const T*>(sr[e].row[1]) + d1);
+        any1 |= (w1[e] != T(0));
+      }
+      if (!any1) continue;
+      for (int d0 = 0; d0 < J0; ++d0) {
+        const int o = d0 + J0 * d1;
+        if (!onz[o]) continue;
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          w[e] = w1[e] * __ldg(static_cast<const T*>(sr[e].row[0]) + d0);
+          any |= (w[e] != T(0));
+        }
+        if (!any) continue;
+        delta_slice<T, JN, JF, E>(d, w, g + o * slice, Jf, rowf, rf);
+      }
+    }
+  } else {
+    int dig[kMaxOrder];
+    for (int i = 0; i < nslow; ++i) dig[i] = 0;
+    for (int64_t o = 0; o < n_outer; ++o) {
+      if (onz[o]) {
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          T x = T(1);
+          for (int i = 0; i < nslow; ++i) x *= __ldg(static_cast<const T*>(sr[e].row[i]) + dig[i]);
+          w[e] = x;
+          any |= (x != T(0));
+        }
+        if (any) delta_slice<T, JN, JF, E>(d, w, g + o * slice, Jf, rowf, rf);
+      }
+      for (int i = 0; i < nslow; ++i) {  // odometer, slow[0] fastest
+        if (++dig[i] < sr[0].J[i]) break;
+        dig[i] = 0;
+      }
+    }
+  }
+}
+
 // Row pointers of the other modes for the entry at CSR position p of mode n.
 // oidx rows are the other modes in ascending order: f first, then the slow ones.
-template <typename T>
+// NSLOW >= 0: the number of slow modes is a compile-time constant (keeps SlowRows in registers).
+template <typename T, int NSLOW = -1>
 __device__ __forceinline__ const T* gather_rows(const DevModel<T>& M, const ModeRoles& r, const int32_t* __restrict__ oidx,
                                                 int64_t nnz, int64_t p, SlowRows& sr) {
   const int64_t i_f = oidx[p];
-  for (int i = 0; i < r.nslow; ++i) {
+  const int ns = NSLOW >= 0 ? NSLOW : r.nslow;
+#pragma unroll
+  for (int i = 0; i < (NSLOW >= 0 ? NSLOW : kMaxOrder); ++i) {
+    if (i >= ns) break;
     const int k = r.slow[i];
     const int64_t ik = oidx[(int64_t)(i + 1) * nnz + p];
     sr.row[i] = M.A[k] + ik * M.J[k];
@@ -194,14 +342,23 @@ __device__ __forceinline__ const T* gather_rows(const DevModel<T>& M, const Mode
 }
 
 // ---------------------------------------------------------------- task -> rows
-// A task is a contiguous range [t0, t1) of positions in a mode's CSR order.
-// loads nzptr[k0 .. k1+1] into sptr; returns the number of rows overlapping it.
-__device__ __forceinline__ int load_task_rows(const int64_t* __restrict__ nzptr, int R, int64_t t0, int64_t t1,
-                                              int64_t* sptr, int64_t* sk0) {
+// A task is a contiguous range [t0, t1) of positions in a mode's CSR order,
+// t0 a multiple of 32.  Loads nzptr[k0 .. k1+1] into sptr and returns the number
+// of rows overlapping the task: k0 from the granule table, k1 from the granule of
+// t1 - 1 plus one warp-wide probe of the (at most 31) row starts after it.
+__device__ __forceinline__ int load_task_rows(const int64_t* __restrict__ nzptr, const int32_t* __restrict__ gran,
+                                              int R, int64_t t0, int64_t t1, int64_t* sptr, int64_t* sk0) {
   __shared__ int64_t k_range[2];
-  if (threadIdx.x == 0) {
-    k_range[0] = upper_bound_m1(nzptr, (int64_t)R, t0);
-    k_range[1] = upper_bound_m1(nzptr, (int64_t)R, t1 - 1);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const int64_t kb = gran[(t1 - 1) >> 5];
+    const int64_t kk = kb + 1 + lane;
+    const bool starts = kk <= R && nzptr[kk] <= t1 - 1;
+    const unsigned bal = __ballot_sync(0xffffffffu, starts);
+    if (lane == 0) {
+      k_range[0] = gran[t0 >> 5];
+      k_range[1] = kb + __popc(bal);
+    }
   }
   __syncthreads();
   const int64_t k0 = k_range[0];
@@ -230,15 +387,28 @@ struct PieceScratch {
   int item0[kMaxLongPieces + 1];   // first item of each long piece
 };
 
+// A term is pa[q * sa] * pb[q * sb] over the piece's task-local entries q.
+template <typename S>
+struct TermPtrs {
+  const S* pa;
+  const S* pb;
+  int sa, sb;
+};
+
 template <typename S, typename F>
-__device__ __forceinline__ S chain_sum(const F& f, const typename F::Prep& pr, int s, int e) {
+__device__ __forceinline__ S chain_sum(const F& f, const TermPtrs<S>& pr, int s, int e) {
+  (void)f;
   S a0 = S(0), a1 = S(0);
+  const S* pa = pr.pa + s * pr.sa;
+  const S* pb = pr.pb + s * pr.sb;
   int q = s;
   for (; q + 1 < e; q += 2) {
-    a0 += f.eval(pr, q);
-    a1 += f.eval(pr, q + 1);
+    a0 += pa[0] * pb[0];
+    a1 += pa[pr.sa] * pb[pr.sb];
+    pa += 2 * pr.sa;
+    pb += 2 * pr.sb;
   }
-  if (q < e) a0 += f.eval(pr, q);
+  if (q < e) a0 += pa[0] * pb[0];
   return a0 + a1;
 }
 

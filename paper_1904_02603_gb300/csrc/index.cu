@@ -278,6 +278,22 @@ __global__ void nzrows_kernel(const uint32_t* __restrict__ skey, int64_t n, cons
   }
 }
 
+// gran[g] = k such that nzptr[k] <= 32 g < nzptr[k + 1] (the non-empty row holding position 32 g)
+__global__ void granule_kernel(const int64_t* __restrict__ nzptr, const int32_t* __restrict__ count, int64_t ng,
+                               int32_t* __restrict__ gran) {
+  const int64_t R = *count;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = g * 32;
+    int64_t lo = 0, hi = R - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (nzptr[mid] <= p) lo = mid;
+      else hi = mid - 1;
+    }
+    gran[g] = (int32_t)lo;
+  }
+}
+
 __global__ void empty_index_kernel(int64_t* nzptr, int32_t* count) {
   nzptr[0] = 0;
   *count = 0;
@@ -330,6 +346,7 @@ IndexLayout layout(const vest_tensor* t) {
     o += align_up((size_t)(cap + 1) * 8);                                          // nzptr
     o += align_up((size_t)std::max<int64_t>(cap, 1) * 4);                          // nzrow
     o += align_up(4);                                                              // count
+    o += align_up((size_t)(ceil_div(std::max<int64_t>(n, 1), 32) + 1) * 4);       // granule rows
     L.mode_bytes[m] = o;
     off += o;
   }
@@ -408,7 +425,8 @@ vest_status build_index_impl(const vest_tensor* t, void* ws, size_t ws_bytes, ve
     mi.val = mb + o; o += align_up((size_t)std::max<int64_t>(n, 1) * (t->val_dtype == VEST_F64 ? 8 : 4));
     mi.nzptr = reinterpret_cast<int64_t*>(mb + o); o += align_up((size_t)(cap + 1) * 8);
     mi.nzrow = reinterpret_cast<int32_t*>(mb + o); o += align_up((size_t)std::max<int64_t>(cap, 1) * 4);
-    mi.nnzrows = reinterpret_cast<int32_t*>(mb + o);
+    mi.nnzrows = reinterpret_cast<int32_t*>(mb + o); o += align_up(4);
+    mi.gran = reinterpret_cast<int32_t*>(mb + o);
     mi.cap = cap;
     if (n == 0) {
       VEST_CUDA(cudaMemsetAsync(mi.row_ptr, 0, (size_t)(t->dims[m] + 1) * 8, s));
@@ -433,6 +451,10 @@ vest_status build_index_impl(const vest_tensor* t, void* ws, size_t ws_bytes, ve
     VEST_TRY(exclusive_scan_i32(flags, pos, n, scan_tmp, s));
     nzrows_kernel<<<grid, 256, 0, s>>>(skey, n, flags, pos, mi.nzptr, mi.nzrow, mi.nnzrows);
     VEST_LAUNCH("nzrows");
+    const int64_t ng = ceil_div(n, 32);
+    granule_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ng, 256), num_sms() * 8)), 256, 0, s>>>(
+        mi.nzptr, mi.nnzrows, ng, mi.gran);
+    VEST_LAUNCH("granule");
     if (t->val_dtype == VEST_F64)
       gather_kernel<double><<<grid, 256, 0, s>>>(t->idx, static_cast<const double*>(t->val), mi.perm, n, N, m,
                                                  mi.oidx, static_cast<double*>(mi.val));

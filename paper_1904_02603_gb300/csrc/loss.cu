@@ -69,13 +69,13 @@ __global__ void __launch_bounds__(kLossTask) loss_kernel(DevModel<T> M, DevMode<
   for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
     const int64_t t0 = task * kLossTask, t1 = min(t0 + (int64_t)kLossTask, nnz);
     int64_t k0;
-    const int nrows = load_task_rows(csr.nzptr, R, t0, t1, sptr, &k0);
+    const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, sptr, &k0);
     const int64_t p = t0 + threadIdx.x;
     if (p < t1) {
       const int lr = local_row(sptr, nrows, p);
       const int64_t i0 = csr.nzrow[k0 + lr];
       SlowRows sr;
-      const T* rowf = gather_rows<T>(M, r, csr.oidx, nnz, p, sr);
+      const T* rowf = gather_rows<T, NSLOW>(M, r, csr.oidx, nnz, p, sr);
       T d[JN];
       compute_delta<T, JN, NSLOW>(d, g, a.onz, r.n_outer, r.Jf, rowf, sr, r.nslow);
       const T* a0 = M.A[0] + i0 * J0;

@@ -3,12 +3,13 @@
 //
 // Work is cut into tasks of TASK consecutive CSR positions (nnz-balanced, so
 // heavy Zipf rows and one-entry rows cost the same per entry):
-//   phase 1  one thread per entry: delta_alpha (Eq. 11) into shared memory;
+//   phase 1  E entries per thread: delta_alpha (Eq. 11) into shared memory,
+//            every core fibre read once for the thread's E entries;
 //   phase 2  the row sums c_j = sum X delta_j and V_jt = sum delta_j delta_t
 //            (Eq. 10) for the update, or sum r delta_j and sum delta_j^2 for the
 //            responsibility, per row piece (accumulator: T): short pieces one
 //            warp each, long pieces cut into 32-entry chunks over all warps and
-//            combined in chunk order;
+//            combined in chunk order; at most KMAX pieces per round;
 //   phase 3  one thread per row: rows that lie inside the task are finished
 //            at once (sequential CD over j, FP64); a row cut by a task edge
 //            writes its piece to a spill slot, and the task where the row
@@ -24,17 +25,13 @@ namespace vest {
 
 enum { kModeUpdate = 0, kModeResp = 1 };
 
-template <typename T>
-struct AccOf {
-  using type = T;
-};
-
 struct SweepArgs {
   ModeRoles r;
   int reg;
   double lambda;
   int64_t ntasks;
-  int task;
+  int task;  // entries per task (blockDim * E)
+  int kmax;  // row pieces per phase-2 round
   int P;
   int use_smem_core;
   const uint8_t* onz;
@@ -92,46 +89,31 @@ __device__ void finish_row(const DevModel<T>& M, int n, int64_t row, const S* su
   }
 }
 
-// Terms of the row sums: update mode c_j = sum X delta_j (p < Jn), then the packed
-// upper Gram delta_j delta_t; responsibility mode sum r delta_j, then sum delta_j^2.
-template <typename T, typename S, int MODE>
+// Terms of the row sums from a per-block table: output p < Jn is X (or r) times
+// delta_j; the rest are delta_j delta_t (packed upper Gram) or delta_j^2.
+template <typename T>
 struct SweepTerm {
   const T* sD;
   const T* sX;
-  int JNS, Jn;
-  struct Prep {
-    int kind, j, t;
-  };
-  __device__ Prep prep(int p) const {
-    if (p < Jn) return Prep{0, p, 0};
-    if constexpr (MODE == kModeUpdate) {
-      int u = p - Jn, j = 0;
-      while (u >= Jn - j) {
-        u -= Jn - j;
-        ++j;
-      }
-      return Prep{1, j, j + u};
-    } else {
-      return Prep{1, p - Jn, p - Jn};
-    }
-  }
-  __device__ S eval(const Prep& pr, int q) const {
-    const T* d = sD + q * JNS;
-    return pr.kind == 0 ? (S)sX[q] * (S)d[pr.j] : (S)d[pr.j] * (S)d[pr.t];
+  const int2* tab;  // (j, t); t < 0: X delta_j
+  int JNS;
+  __device__ TermPtrs<T> prep(int p) const {
+    const int2 jt = tab[p];
+    if (jt.y < 0) return TermPtrs<T>{sX, sD + jt.x, 1, JNS};
+    return TermPtrs<T>{sD + jt.x, sD + jt.y, JNS, JNS};
   }
 };
 
-template <typename T, int JN, int NSLOW, int MODE>
+template <typename T, int JN, int JF, int NSLOW, int MODE, int E>
 __global__ void __launch_bounds__(256) sweep_task_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ gcore,
                                                          SweepArgs a) {
-  using S = typename AccOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ModeRoles& r = a.r;
-  const int TASK = a.task;
+  const int TASK = a.task, KMAX = a.kmax;
   const int JNS = JN + 1;
   const int P = a.P;
   const int64_t core_elems = r.n_outer * r.Jf * JN;
-  // shared layout: core | sptr | D | X | acc
+  // shared layout: core | sptr | D | X | acc | long-piece partials | term table
   T* sG = reinterpret_cast<T*>(smem_raw);
   size_t off = a.use_smem_core ? (size_t)core_elems * sizeof(T) : 0;
   off = (off + 15) & ~(size_t)15;
@@ -142,9 +124,11 @@ __global__ void __launch_bounds__(256) sweep_task_kernel(DevModel<T> M, DevMode<
   T* sX = reinterpret_cast<T*>(smem_raw + off);
   off += (size_t)TASK * sizeof(T);
   off = (off + 15) & ~(size_t)15;
-  S* sAcc = reinterpret_cast<S*>(smem_raw + off);
-  off += (size_t)TASK * P * sizeof(S);
-  S* sPart = reinterpret_cast<S*>(smem_raw + off);
+  T* sAcc = reinterpret_cast<T*>(smem_raw + off);
+  off += (size_t)KMAX * P * sizeof(T);
+  T* sPart = reinterpret_cast<T*>(smem_raw + off);
+  off += (size_t)kMaxLongPieces * P * sizeof(T);
+  int2* sTab = reinterpret_cast<int2*>(smem_raw + off);
   __shared__ PieceScratch pscr;
 
   const T* g = gcore;
@@ -152,52 +136,78 @@ __global__ void __launch_bounds__(256) sweep_task_kernel(DevModel<T> M, DevMode<
     for (int64_t e = threadIdx.x; e < core_elems; e += blockDim.x) sG[e] = gcore[e];
     g = sG;
   }
-  const int R = *csr.nnzrows;
-  const int64_t nnz = csr.nnz;
   const int n = r.n;
   const int Jn = r.Jn;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    if (p < Jn) {
+      sTab[p] = make_int2(p, -1);
+    } else if constexpr (MODE == kModeUpdate) {
+      int u = p - Jn, j = 0;
+      while (u >= Jn - j) {
+        u -= Jn - j;
+        ++j;
+      }
+      sTab[p] = make_int2(j, j + u);
+    } else {
+      sTab[p] = make_int2(p - Jn, p - Jn);
+    }
+  }
+  const int R = *csr.nnzrows;
+  const int64_t nnz = csr.nnz;
   __syncthreads();
 
   for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
     const int64_t t0 = task * TASK, t1 = min(t0 + (int64_t)TASK, nnz);
     const int cnt = (int)(t1 - t0);
     int64_t k0;
-    const int nrows = load_task_rows(csr.nzptr, R, t0, t1, sptr, &k0);
+    const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, sptr, &k0);
 
-    // phase 1: delta per entry
+    // phase 1: delta for the thread's E entries (threadIdx.x + e * blockDim.x)
     if ((int)threadIdx.x < cnt) {
-      const int64_t p = t0 + threadIdx.x;
-      SlowRows sr;
-      const T* rowf = gather_rows<T>(M, r, csr.oidx, nnz, p, sr);
-      T d[JN];
-      compute_delta<T, JN, NSLOW>(d, g, a.onz, r.n_outer, r.Jf, rowf, sr, r.nslow);
-      T* dst = sD + threadIdx.x * JNS;
+      const T* rowf[E];
+      SlowRows sr[E];
 #pragma unroll
-      for (int j = 0; j < JN; ++j) dst[j] = d[j];
-      if constexpr (MODE == kModeUpdate) sX[threadIdx.x] = csr.val[p];
-      else sX[threadIdx.x] = static_cast<const T*>(a.resid_coo)[csr.perm[p]];
-    }
-    __syncthreads();
-
-    // phase 2: per-row sums over the task's piece of the row
-    {
-      SweepTerm<T, S, MODE> f{sD, sX, JNS, Jn};
-      piece_sums<S>(sptr, nrows, t0, t1, P, sAcc, sPart, &pscr, f);
-    }
-
-    // phase 3: finish whole rows, spill cut ones
-    for (int k = threadIdx.x; k < nrows; k += blockDim.x) {
-      const int64_t rs = sptr[k], re = sptr[k + 1];
-      if (rs >= t0 && re <= t1) {
-        finish_row<T, S, MODE>(M, n, (int64_t)csr.nzrow[k0 + k], sAcc + k * P, a);
-      } else {
-        const int slot = (k == 0) ? 0 : 1;
-        double* sp = a.spill + ((size_t)task * 2 + slot) * P;
-        for (int i = 0; i < P; ++i) sp[i] = (double)sAcc[k * P + i];
+      for (int e = 0; e < E; ++e) {
+        const int q = threadIdx.x + e * blockDim.x;
+        const int64_t p = t0 + (q < cnt ? q : (int)threadIdx.x);
+        rowf[e] = gather_rows<T, NSLOW>(M, r, csr.oidx, nnz, p, sr[e]);
       }
-      if (k == nrows - 1) a.spanning[task] = (rs >= t0 && re > t1) ? (int32_t)(k0 + k) : -1;
+      T d[E][JN];
+      compute_delta_multi<T, JN, JF, NSLOW, E>(d, g, a.onz, r.n_outer, r.Jf, rowf, sr, r.nslow);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int q = threadIdx.x + e * blockDim.x;
+        if (q < cnt) {
+          T* dst = sD + q * JNS;
+#pragma unroll
+          for (int j = 0; j < JN; ++j) dst[j] = d[e][j];
+          if constexpr (MODE == kModeUpdate) sX[q] = csr.val[t0 + q];
+          else sX[q] = static_cast<const T*>(a.resid_coo)[csr.perm[t0 + q]];
+        }
+      }
     }
     __syncthreads();
+
+    const SweepTerm<T> f{sD, sX, sTab, JNS};
+    for (int r0 = 0; r0 < nrows; r0 += KMAX) {
+      const int nr = min(KMAX, nrows - r0);
+      // phase 2: per-row sums over the task's pieces r0 .. r0 + nr - 1
+      piece_sums<T>(sptr + r0, nr, t0, t1, P, sAcc, sPart, &pscr, f);
+      // phase 3: finish whole rows, spill cut ones
+      for (int kr = threadIdx.x; kr < nr; kr += blockDim.x) {
+        const int k = r0 + kr;
+        const int64_t rs = sptr[k], re = sptr[k + 1];
+        if (rs >= t0 && re <= t1) {
+          finish_row<T, T, MODE>(M, n, (int64_t)csr.nzrow[k0 + k], sAcc + kr * P, a);
+        } else {
+          const int slot = (k == 0) ? 0 : 1;
+          double* sp = a.spill + ((size_t)task * 2 + slot) * P;
+          for (int i = 0; i < P; ++i) sp[i] = (double)sAcc[kr * P + i];
+        }
+        if (k == nrows - 1) a.spanning[task] = (rs >= t0 && re > t1) ? (int32_t)(k0 + k) : -1;
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -261,77 +271,82 @@ __global__ void empty_rows_kernel(DevModel<T> M, int n, const int64_t* __restric
 }
 
 // ------------------------------------------------------------------ host side
-template <typename T>
 static int outputs_per_row(int Jn, int mode_kind) {
   return mode_kind == kModeUpdate ? Jn + Jn * (Jn + 1) / 2 : 2 * Jn;
 }
 
 constexpr size_t kSmemBudget = 200 * 1024;
+constexpr size_t kAccBudget = 32 * 1024;
+constexpr int kTask = 256;
 
 template <typename T>
-static size_t task_smem(int task, int JN, int P, size_t core_bytes) {
+static int pieces_per_round(int P) {
+  return (int)std::max<size_t>(1, std::min<size_t>(64, kAccBudget / ((size_t)P * sizeof(T))));
+}
+
+template <typename T>
+static size_t task_smem(int task, int kmax, int JN, int P, size_t core_bytes) {
   size_t off = (core_bytes + 15) & ~(size_t)15;
   off += (size_t)(task + 2) * 8;
   off += (size_t)task * (JN + 1) * sizeof(T);
   off += (size_t)task * sizeof(T);
   off = (off + 15) & ~(size_t)15;
-  off += (size_t)task * P * sizeof(typename AccOf<T>::type);
-  off += (size_t)kMaxLongPieces * P * sizeof(typename AccOf<T>::type);
+  off += (size_t)kmax * P * sizeof(T);
+  off += (size_t)kMaxLongPieces * P * sizeof(T);
+  off += (size_t)P * sizeof(int2);
   return off;
 }
 
-// Task size used for a mode: the largest of 256/128/64/32 whose shared memory fits
-// (the core is placed in shared memory only when it leaves room for >= 64-entry tasks).
+// Task geometry: 256 entries per task; the core goes to shared memory when it fits.
 template <typename T>
 int sweep_task_size(int Jn, int P, int64_t core_elems, int* use_smem_core) {
   const int JN = jn_bucket(Jn);
-  const size_t core_bytes = (size_t)core_elems * sizeof(T);
-  for (int pass = 0; pass < 2; ++pass) {
-    const size_t cb = pass == 0 ? core_bytes : 0;
-    for (int task = 256; task >= 32; task >>= 1) {
-      if (pass == 0 && task < 64) break;
-      if (task_smem<T>(task, JN, P, cb) <= kSmemBudget) {
-        *use_smem_core = pass == 0;
-        return task;
-      }
-    }
-  }
-  *use_smem_core = 0;
-  return 32;
+  *use_smem_core = task_smem<T>(kTask, pieces_per_round<T>(P), JN, P, (size_t)core_elems * sizeof(T)) <= kSmemBudget;
+  return kTask;
 }
 
 template int sweep_task_size<float>(int, int, int64_t, int*);
 template int sweep_task_size<double>(int, int, int64_t, int*);
 
-template <typename T, int JN, int NSLOW, int MODE>
+template <typename T, int JN, int JF, int NSLOW, int MODE, int E>
 static vest_status launch_task(const DevModel<T>& M, const DevMode<T>& csr, const T* gp, const SweepArgs& a,
                                size_t smem, cudaStream_t s) {
-  auto kern = sweep_task_kernel<T, JN, NSLOW, MODE>;
+  auto kern = sweep_task_kernel<T, JN, JF, NSLOW, MODE, E>;
   VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t grid = std::min<int64_t>(a.ntasks, (int64_t)num_sms() * 16);
-  kern<<<(unsigned)std::max<int64_t>(grid, 1), a.task, smem, s>>>(M, csr, gp, a);
+  kern<<<(unsigned)std::max<int64_t>(grid, 1), a.task / E, smem, s>>>(M, csr, gp, a);
   VEST_LAUNCH("sweep_task_kernel");
   return VEST_OK;
 }
 
+// FP32: two entries per thread, the f-mode rank in registers when it equals the
+// bucket width; FP64 (the accuracy reference path): one entry per thread.
 template <typename T, int JN, int MODE>
-static vest_status dispatch_nslow(int nslow, const DevModel<T>& M, const DevMode<T>& csr, const T* gp,
+static vest_status dispatch_nslow(int nslow, int Jf, const DevModel<T>& M, const DevMode<T>& csr, const T* gp,
                                   const SweepArgs& a, size_t smem, cudaStream_t s) {
-  if (MODE == kModeUpdate && nslow == 1) return launch_task<T, JN, 1, MODE>(M, csr, gp, a, smem, s);
-  if (MODE == kModeUpdate && nslow == 2) return launch_task<T, JN, 2, MODE>(M, csr, gp, a, smem, s);
-  return launch_task<T, JN, -1, MODE>(M, csr, gp, a, smem, s);
+  if constexpr (sizeof(T) == 4) {
+    if (nslow == 1 && Jf == JN) return launch_task<T, JN, JN, 1, MODE, 2>(M, csr, gp, a, smem, s);
+    if (nslow == 1) return launch_task<T, JN, 0, 1, MODE, 2>(M, csr, gp, a, smem, s);
+    if (nslow == 2 && Jf == JN) return launch_task<T, JN, JN, 2, MODE, 2>(M, csr, gp, a, smem, s);
+    if (nslow == 2) return launch_task<T, JN, 0, 2, MODE, 2>(M, csr, gp, a, smem, s);
+    return launch_task<T, JN, 0, -1, MODE, 1>(M, csr, gp, a, smem, s);
+  } else {
+    if (nslow == 1) return launch_task<T, JN, 0, 1, MODE, 1>(M, csr, gp, a, smem, s);
+    if (nslow == 2) return launch_task<T, JN, 0, 2, MODE, 1>(M, csr, gp, a, smem, s);
+    return launch_task<T, JN, 0, -1, MODE, 1>(M, csr, gp, a, smem, s);
+  }
 }
 
 template <typename T, int MODE>
-static vest_status dispatch_jn(int JN, int nslow, const DevModel<T>& M, const DevMode<T>& csr, const T* gp,
+static vest_status dispatch_jn(int JN, int nslow, int Jf, const DevModel<T>& M, const DevMode<T>& csr, const T* gp,
                                const SweepArgs& a, size_t smem, cudaStream_t s) {
   switch (JN) {
-    case 4: return dispatch_nslow<T, 4, MODE>(nslow, M, csr, gp, a, smem, s);
-    case 8: return dispatch_nslow<T, 8, MODE>(nslow, M, csr, gp, a, smem, s);
-    case 10: return dispatch_nslow<T, 10, MODE>(nslow, M, csr, gp, a, smem, s);
-    case 12: return dispatch_nslow<T, 12, MODE>(nslow, M, csr, gp, a, smem, s);
-    case 16: return dispatch_nslow<T, 16, MODE>(nslow, M, csr, gp, a, smem, s);
-    default: return dispatch_nslow<T, 32, MODE>(nslow, M, csr, gp, a, smem, s);
+    case 4: return dispatch_nslow<T, 4, MODE>(nslow, Jf, M, csr, gp, a, smem, s);
+    case 8: return dispatch_nslow<T, 8, MODE>(nslow, Jf, M, csr, gp, a, smem, s);
+    case 10: return dispatch_nslow<T, 10, MODE>(nslow, Jf, M, csr, gp, a, smem, s);
+    case 12: return dispatch_nslow<T, 12, MODE>(nslow, Jf, M, csr, gp, a, smem, s);
+    case 16: return dispatch_nslow<T, 16, MODE>(nslow, Jf, M, csr, gp, a, smem, s);
+    default: return dispatch_nslow<T, 32, MODE>(nslow, Jf, M, csr, gp, a, smem, s);
   }
 }
 
@@ -349,9 +364,10 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
   prep_core_kernel<T><<<(unsigned)std::min<int64_t>(r.n_outer, 4096), 128, 0, s>>>(M.G, r, JN, gp, onz);
   VEST_LAUNCH("prep_core_kernel");
   a.onz = onz;
-  a.P = outputs_per_row<T>(r.Jn, MODE);
+  a.P = outputs_per_row(r.Jn, MODE);
   int use_smem = 0;
   a.task = sweep_task_size<T>(r.Jn, a.P, core_elems, &use_smem);
+  a.kmax = pieces_per_round<T>(a.P);
   a.use_smem_core = use_smem;
   a.ntasks = ceil_div(ix->nnz, a.task);
   if ((size_t)a.ntasks * 2 * a.P * 8 > plan.spill_bytes || a.ntasks > plan.ntasks)
@@ -363,8 +379,8 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
   empty_rows_kernel<T, MODE><<<eg, 256, 0, s>>>(M, n, ix->mode[n].row_ptr, a.delta, a.resp);
   VEST_LAUNCH("empty_rows_kernel");
   if (ix->nnz == 0) return VEST_OK;
-  const size_t smem = task_smem<T>(a.task, JN, a.P, use_smem ? (size_t)core_elems * sizeof(T) : 0);
-  VEST_TRY(dispatch_jn<T, MODE>(JN, r.nslow, M, csr, gp, a, smem, s));
+  const size_t smem = task_smem<T>(a.task, a.kmax, JN, a.P, use_smem ? (size_t)core_elems * sizeof(T) : 0);
+  VEST_TRY(dispatch_jn<T, MODE>(JN, r.nslow, r.Jf, M, csr, gp, a, smem, s));
   const size_t fsmem = (size_t)std::max(1, 256 / a.P) * a.P * 8 + 8 * a.P;
   auto fk = sweep_fixup_kernel<T, MODE>;
   VEST_CUDA(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));

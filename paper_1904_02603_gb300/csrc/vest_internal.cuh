@@ -53,6 +53,7 @@ struct ModeIndex {
   int64_t* nzptr;    // [cap + 1]
   int32_t* nzrow;    // [cap]
   int32_t* nnzrows;  // device scalar R_n
+  int32_t* gran;     // [ceil(nnz/32) + 1]: non-empty-row number k holding position 32 g
   int64_t cap;       // min(I_n, nnz)
 };
 
@@ -105,6 +106,7 @@ struct DevMode {
   const int64_t* nzptr;
   const int32_t* nzrow;
   const int32_t* nnzrows;
+  const int32_t* gran;
   const int32_t* oidx;  // [(N-1)][nnz]
   const T* val;
   const int32_t* perm;
@@ -118,6 +120,7 @@ inline DevMode<T> dev_mode(const vest_index* ix, int n) {
   d.nzptr = mi.nzptr;
   d.nzrow = mi.nzrow;
   d.nnzrows = mi.nnzrows;
+  d.gran = mi.gran;
   d.oidx = mi.oidx;
   d.val = static_cast<const T*>(mi.val);
   d.perm = mi.perm;
