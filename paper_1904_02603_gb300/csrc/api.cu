@@ -11,7 +11,8 @@
 
 namespace vest {
 
-size_t core_part_bytes(const vest_model* m);
+size_t core_scratch_bytes(const vest_model* m, int64_t nnz, int64_t cap0, size_t* y_bytes, size_t* gram_bytes,
+                          size_t* part_bytes);
 size_t loss_part_bytes();
 size_t normalize_scratch_bytes();
 size_t prune_scratch_bytes(int64_t maxseg, size_t* keys_bytes, size_t* vals_bytes, size_t* tmp_bytes);
@@ -115,7 +116,7 @@ ScratchPlan plan_scratch(const vest_index* ix, const vest_model* m) {
   p.ntasks = nt;
   p.off_resid = o; o += align_up((size_t)std::max<int64_t>(ix->nnz, 1) * sT);
   p.off_resid_coo = o; o += align_up((size_t)std::max<int64_t>(ix->nnz, 1) * sT);
-  p.part_bytes = align_up(std::max({core_part_bytes(m), loss_part_bytes(), normalize_scratch_bytes()}));
+  p.part_bytes = align_up(std::max(loss_part_bytes(), normalize_scratch_bytes()));
   p.off_part = o; o += p.part_bytes;
   p.off_small = o; o += 128 * 1024;
   size_t kb, vb, tb;
@@ -123,6 +124,9 @@ ScratchPlan plan_scratch(const vest_index* ix, const vest_model* m) {
   p.off_prune_keys = o; o += kb;
   p.off_prune_vals = o; o += vb;
   p.off_prune_tmp = o; o += tb;
+  size_t yb, gb, cpb;
+  const int64_t cap0 = std::min<int64_t>(ix->dims[0], std::max<int64_t>(ix->nnz, 1));
+  p.off_core = o; o += align_up(core_scratch_bytes(m, ix->nnz, cap0, &yb, &gb, &cpb));
   p.total = o;
   return p;
 }

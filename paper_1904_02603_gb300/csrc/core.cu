@@ -5,20 +5,23 @@
 // as the paper requires (Section 3.6).  On the GPU this is blocked
 // Gauss-Seidel, equal to the one-at-a-time sweep in exact arithmetic:
 //   - a block is b = J_0 * m consecutive core elements, (j_0, j_1) in
-//     J_0 x [q0, q0 + m) for one fixed suffix (j_2, ..., j_{N-1});
-//   - one pass over the mode-0 CSR computes, from the residual r at the block
-//     start, g_k = sum_alpha r_alpha P_alpha(k) and the block Gram
-//     M_kl = sum_alpha P_alpha(k) P_alpha(l), with P_alpha(j_0, j_1) =
-//     a0[i_0, j_0] * a1[i_1, j_1] * c_alpha and c_alpha = prod_{n>=2}
-//     a_n[i_n, s_n].  Entries are grouped by their mode-0 row, so per row
-//     piece only Q = sum w w^T and h = sum r w with w(q) = a1[i_1, q0+q] c_alpha
-//     are formed, and M += (a0 a0^T) (x) Q, g += a0 (x) h;
-//   - one thread block then runs the b updates in order exactly:
-//     sum_alpha r_alpha P_alpha(k) at step k is g_k - sum_{l<k} Delta_l M_lk;
-//   - the next pass first applies this block's Delta to r.
-// Per-block sums: per piece in the storage type, across pieces in a
-// Kahan-compensated accumulator (FP32) or FP64, across thread blocks in FP64
-// in a fixed order.
+//     J_0 x [q0, q0 + m) for one suffix s = (j_2, ..., j_{N-1});
+//     P_alpha(j_0, j_1) = a0[i_0, j_0] * a1[i_1, j_1] * c_alpha(s), with
+//     c_alpha(s) = prod_{n>=2} a_n[i_n, s_n];
+//   - the block Grams M_b = sum_alpha P_alpha P_alpha^T depend on the factors
+//     only, which the core sweep does not change, so all of them are formed
+//     first.  Entries are grouped by their mode-0 row piece (row within a task):
+//     a gram pass writes per piece Y(s, q, q') = sum c(s)^2 a1[q] a1[q'], a tiled
+//     reduction over pieces forms Z(s) = sum_piece sym(a0 a0^T) (x) Y(s), and a
+//     merge expands Z into each packed M_b in FP64;
+//   - then per block in order: one pass over the mode-0 CSR applies the
+//     previous block's Delta to r and forms g_k = sum_alpha r_alpha P_alpha(k)
+//     (per piece h(q) = sum r w(q), g += a0 (x) h); one thread block performs
+//     the b updates in order with sum_alpha r P(k) = g_k - sum_{l<k} Delta_l M_lk.
+// The core responsibility needs g and diag(M) of every element for a fixed r:
+// one stats pass per group of suffixes.
+// Sums: per piece in the storage type; across pieces and tasks FP32 with Kahan
+// compensation (or FP64); across thread blocks FP64 in a fixed order.
 #include <algorithm>
 
 #include "delta.cuh"
@@ -28,40 +31,17 @@ namespace vest {
 constexpr int kCoreTask = 256;
 constexpr int kCoreMaxB = 128;
 constexpr int kCoreMaxM = 10;
-constexpr int kCoreEPT = 24;           // accumulator entries per thread (nz <= 5408 for b <= 128, m <= 10)
-constexpr int kCorePassCtas = 296;     // fixed: reduction order does not depend on the device
+constexpr int kGramMaxP = 576;      // per-piece gram outputs per group
+constexpr int kGramKSplit = 64;     // fixed: reduction order does not depend on the device
+constexpr int kCorePassCtas = 296;  // fixed likewise
+constexpr int kStatsEPT = 16;       // stats accumulators per thread
+constexpr int kCoreKmax = 64;       // row pieces per phase-2 round
 
 struct CoreBlock {
-  int64_t s;      // suffix linear index over modes >= 2
-  int q0, m;      // j_1 range
-  int b;          // J_0 * m
+  int64_t s;  // suffix linear index over modes >= 2
+  int q0, m;  // j_1 range
+  int b;      // J_0 * m
 };
-
-struct CoreArgs {
-  int N, J0, J1;
-  int64_t nnz;
-  int64_t ntasks;
-  CoreBlock cur, prev;
-  int has_prev;
-  int nent;               // b(b+1)/2 + b entries of the packed Gram and g
-  int nz;                 // Kronecker-form accumulator entries
-  const double* dprev;    // Delta of the previous block [b_prev]
-  double* part;           // [ctas][nent]
-};
-
-// c_alpha for a suffix s: prod over modes n >= 2 of a_n[i_n, digit_n(s)]
-template <typename T>
-__device__ __forceinline__ T suffix_weight(const DevModel<T>& M, const int32_t* __restrict__ oidx, int64_t nnz, int64_t p,
-                                           int64_t s) {
-  T c = T(1);
-  for (int n = 2; n < M.N; ++n) {
-    const int d = (int)(s % M.J[n]);
-    s /= M.J[n];
-    const int64_t in = oidx[(int64_t)(n - 1) * nnz + p];  // mode-0 CSR: oidx rows are modes 1..N-1
-    c *= M.A[n][in * M.J[n] + d];
-  }
-  return c;
-}
 
 // Running sums across tasks: Kahan-compensated for FP32, plain for FP64.
 template <typename T>
@@ -82,104 +62,284 @@ struct CoreAcc<double> {
   static __device__ double value(double s, double) { return s; }
 };
 
-// entry e of the packed accumulator -> (k, l): e < b(b+1)/2 packed upper M (k <= l), else g_k
-__device__ __forceinline__ void entry_kl(int e, int b, int& k, int& l) {
-  const int nm = b * (b + 1) / 2;
-  if (e >= nm) {
-    k = e - nm;
-    l = -1;
-    return;
-  }
-  int kk = 0, u = e;
-  while (u >= b - kk) {
-    u -= b - kk;
-    ++kk;
-  }
-  k = kk;
-  l = kk + u;
+__host__ __device__ __forceinline__ int sym_index(int x, int y, int n) {
+  const int lo = x < y ? x : y, hi = x < y ? y : x;
+  return lo * n - (lo * (lo - 1)) / 2 + (hi - lo);
 }
 
-// Terms of the per-piece sums: packed upper Q = sum w w^T, then h = sum r w.
-template <typename T>
-struct CoreTerm {
-  const T* sW;
-  const T* sR;
-  int m;
-  __device__ TermPtrs<T> prep(int p) const {
-    const int nq = m * (m + 1) / 2;
-    if (p >= nq) return TermPtrs<T>{sR, sW + (p - nq), 1, m};
-    int u = p, q = 0;
-    while (u >= m - q) {
-      u -= m - q;
-      ++q;
-    }
-    return TermPtrs<T>{sW + q, sW + q + u, m, m};
+__device__ __forceinline__ void sym_decode(int u, int n, int& a, int& b) {
+  int k = 0;
+  while (u >= n - k) {
+    u -= n - k;
+    ++k;
   }
+  a = k;
+  b = k + u;
+}
+
+// entry e of a packed upper b x b matrix -> (k, l), k <= l
+__device__ __forceinline__ void entry_kl(int e, int b, int& k, int& l) { sym_decode(e, b, k, l); }
+
+// c_alpha(s) for the `count` consecutive suffixes starting at s0 (mode 2 fastest)
+template <typename T>
+__device__ __forceinline__ void suffix_weights(const DevModel<T>& M, const int32_t* __restrict__ oidx, int64_t nnz,
+                                               int64_t p, int64_t s0, int count, T* out, int stride) {
+  if (M.N == 2) {
+    for (int i = 0; i < count; ++i) out[i * stride] = T(1);
+    return;
+  }
+  if (M.N == 3) {
+    const T* row = M.A[2] + (int64_t)oidx[nnz + p] * M.J[2] + s0;
+    for (int i = 0; i < count; ++i) out[i * stride] = row[i];
+    return;
+  }
+  const T* rows[kMaxOrder];
+  int dig[kMaxOrder];
+  int64_t rem = s0;
+  for (int n = 2; n < M.N; ++n) {
+    rows[n] = M.A[n] + (int64_t)oidx[(int64_t)(n - 1) * nnz + p] * M.J[n];
+    dig[n] = (int)(rem % M.J[n]);
+    rem /= M.J[n];
+  }
+  for (int i = 0; i < count; ++i) {
+    T c = T(1);
+    for (int n = 2; n < M.N; ++n) c *= rows[n][dig[n]];
+    out[i * stride] = c;
+    for (int n = 2; n < M.N; ++n) {
+      if (++dig[n] < M.J[n]) break;
+      dig[n] = 0;
+    }
+  }
+}
+
+// ================================================================== gram pass
+struct GramArgs {
+  int J0, J1;
+  int q0, mq, nY;
+  int64_t s0;
+  int Sg, P, kmax;
+  int64_t nnz, ntasks;
+  void* Y;         // [slots][P]
+  int32_t* srow;   // [slots]: compacted mode-0 row of the slot, -1 if unused
+};
+
+// terms of the gram pass: p = sidx * nY + yi -> c(s)^2 * K(yi)
+template <typename T>
+struct GramTerm {
+  const T* sC;  // [entry][Sg]
+  const T* sK;  // [entry][nY]
+  int Sg, nY;
+  __device__ TermPtrs<T> prep(int p) const { return TermPtrs<T>{sC + p / nY, sK + p % nY, Sg, nY}; }
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kCoreTask) core_pass_kernel(DevModel<T> M, DevMode<T> csr, const T* r_in,
-                                                              T* r_out, CoreArgs a) {
+__global__ void __launch_bounds__(kCoreTask) core_gram_pass_kernel(DevModel<T> M, DevMode<T> csr, GramArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int J0 = a.J0, m = a.cur.m, b = a.cur.b;
-  const int mp = a.has_prev ? a.prev.m : 0;
-  const int QP = m * (m + 1) / 2 + m;
+  const int P = a.P, nY = a.nY, Sg = a.Sg, mq = a.mq;
   size_t off = 0;
   int64_t* sptr = reinterpret_cast<int64_t*>(smem_raw + off); off += (size_t)(kCoreTask + 2) * 8;
-  double* sdp = reinterpret_cast<double*>(smem_raw + off); off += (size_t)kCoreMaxB * 8;
-  T* sA0 = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * J0 * sizeof(T);
-  T* sU = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * max(mp, 1) * sizeof(T);
-  T* sW = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * m * sizeof(T);
-  T* sR = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * sizeof(T);
-  T* sQ = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * QP * sizeof(T);
-  T* sPart = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kMaxLongPieces * QP * sizeof(T);
-  T* sSum = reinterpret_cast<T*>(smem_raw + off); off += (size_t)a.nz * sizeof(T);
-  T* sComp = reinterpret_cast<T*>(smem_raw + off);
+  T* sK = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * nY * sizeof(T);
+  T* sC = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * Sg * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  T* sAcc = reinterpret_cast<T*>(smem_raw + off); off += (size_t)a.kmax * P * sizeof(T);
+  T* sPart = reinterpret_cast<T*>(smem_raw + off);
   __shared__ PieceScratch pscr;
-
-  if (a.has_prev)
-    for (int i = threadIdx.x; i < a.prev.b; i += blockDim.x) sdp[i] = a.dprev[i];
-
-  // Block Gram in Kronecker form: Z[xi][yi] = sum over row pieces of
-  // X[xi] * Y[yi], X = packed upper a0 a0^T (nX = J0(J0+1)/2 values), Y = packed
-  // upper Q (nY = m(m+1)/2), followed by the J0*m products a0[j0] * h[q] of g.
-  // Each thread owns entries threadIdx.x + i * blockDim.x, coded as
-  // a0 index 1 (8 bits) | a0 index 2 (8 bits, 255 = g entry) | offset into Q/h (16 bits).
-  T tacc[kCoreEPT];
-  uint32_t code[kCoreEPT];
-  int nown = 0;
-  const int nY = m * (m + 1) / 2, nX = J0 * (J0 + 1) / 2;
-#pragma unroll
-  for (int i = 0; i < kCoreEPT; ++i) {
-    code[i] = 0xFFFFFFFFu;
-    const int e = threadIdx.x + i * blockDim.x;
-    if (e < a.nz) {
-      if (e < nX * nY) {
-        int u = e / nY, ja = 0;
-        while (u >= J0 - ja) {
-          u -= J0 - ja;
-          ++ja;
-        }
-        code[i] = (uint32_t)ja | ((uint32_t)(ja + u) << 8) | ((uint32_t)(e % nY) << 16);
-      } else {
-        const int g = e - nX * nY;
-        code[i] = (uint32_t)(g % J0) | (255u << 8) | ((uint32_t)(nY + g / J0) << 16);
-      }
-      nown = i + 1;
-      sSum[e] = T(0);
-      sComp[e] = T(0);
-    }
-  }
   const int R = *csr.nnzrows;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  __syncthreads();
-
+  T* Y = static_cast<T*>(a.Y);
   for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
     const int64_t t0 = task * kCoreTask, t1 = min(t0 + (int64_t)kCoreTask, a.nnz);
     const int cnt = (int)(t1 - t0);
     int64_t k0;
     const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, sptr, &k0);
-    // row data: a0 row and u(q) = sum_j0 Delta_prev(j0, q) a0[j0]
+    if ((int)threadIdx.x < cnt) {
+      const int64_t p = t0 + threadIdx.x;
+      const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * a.J1 + a.q0;
+      T v[kCoreMaxM];
+#pragma unroll
+      for (int q = 0; q < kCoreMaxM; ++q) v[q] = q < mq ? a1[q] : T(0);
+      T* k = sK + threadIdx.x * nY;
+      int yi = 0;
+#pragma unroll
+      for (int q = 0; q < kCoreMaxM; ++q)
+#pragma unroll
+        for (int q2 = q; q2 < kCoreMaxM; ++q2)
+          if (q2 < mq) k[yi++] = v[q] * v[q2];
+      T* c = sC + threadIdx.x * Sg;
+      suffix_weights<T>(M, csr.oidx, a.nnz, p, a.s0, Sg, c, 1);
+      for (int i = 0; i < Sg; ++i) c[i] *= c[i];
+    }
+    __syncthreads();
+    const GramTerm<T> f{sC, sK, Sg, nY};
+    for (int r0 = 0; r0 < nrows; r0 += a.kmax) {
+      const int nr = min(a.kmax, nrows - r0);
+      piece_sums<T>(sptr + r0, nr, t0, t1, P, sAcc, sPart, &pscr, f);
+      for (int kr = 0; kr < nr; ++kr) {
+        const int64_t slot = k0 + r0 + kr + task;
+        for (int pp = threadIdx.x; pp < P; pp += blockDim.x) Y[slot * P + pp] = sAcc[kr * P + pp];
+        if (threadIdx.x == 0) a.srow[slot] = (int32_t)(k0 + r0 + kr);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Z[ks][xi][p] = sum over the slots of split ks of X_slot[xi] * Y[slot][p], X = packed
+// upper a0 a0^T of the slot's row.  Tile 32 (xi) x 64 (p); 32-slot chunks in FP32,
+// Kahan across chunks.
+struct GemmArgs {
+  int J0, nX, P;
+  int64_t nslots;
+  const void* Y;
+  const int32_t* srow;
+  double* part;  // [ks][nX][P]
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) core_gram_gemm_kernel(DevModel<T> M, DevMode<T> csr, GemmArgs a) {
+  __shared__ T sX[32][33];
+  __shared__ T sY[32][65];
+  __shared__ int2 xtab[32];
+  const int tiles_p = (a.P + 63) / 64;
+  const int tx0 = (blockIdx.x / tiles_p) * 32, tp0 = (blockIdx.x % tiles_p) * 64;
+  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+  const int ks = blockIdx.y;
+  const int64_t per = ceil_div(a.nslots, (int64_t)gridDim.y);
+  const int64_t sl0 = ks * per, sl1 = min(a.nslots, sl0 + per);
+  if (threadIdx.x < 32) {
+    const int xi = tx0 + threadIdx.x;
+    int ja = 0, jb = 0;
+    if (xi < a.nX) sym_decode(xi, a.J0, ja, jb);
+    xtab[threadIdx.x] = make_int2(xi < a.nX ? ja : -1, jb);
+  }
+  const T* Y = static_cast<const T*>(a.Y);
+  T run_s[4][2], run_c[4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) run_s[i][j] = run_c[i][j] = T(0);
+  __syncthreads();
+  for (int64_t c0 = sl0; c0 < sl1; c0 += 32) {
+    // stage 32 slots: X from the slot's a0 row, Y tile
+    for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+      const int cs = i >> 5, xl = i & 31;
+      const int64_t slot = c0 + cs;
+      T xv = T(0);
+      const int2 jt = xtab[xl];
+      if (slot < sl1 && jt.x >= 0) {
+        const int32_t k = a.srow[slot];
+        if (k >= 0) {
+          const T* a0 = M.A[0] + (int64_t)csr.nzrow[k] * a.J0;
+          xv = a0[jt.x] * a0[jt.y];
+        }
+      }
+      sX[cs][xl] = xv;
+    }
+    for (int i = threadIdx.x; i < 32 * 64; i += blockDim.x) {
+      const int cs = i >> 6, pl = i & 63;
+      const int64_t slot = c0 + cs;
+      const int p = tp0 + pl;
+      T yv = T(0);
+      if (slot < sl1 && p < a.P && a.srow[slot] >= 0) yv = Y[slot * a.P + p];
+      sY[cs][pl] = yv;
+    }
+    __syncthreads();
+    T acc[4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) acc[i][j] = T(0);
+#pragma unroll 8
+    for (int cs = 0; cs < 32; ++cs) {
+      T xv[4], yv[2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xv[i] = sX[cs][ty + 8 * i];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) yv[j] = sY[cs][tx + 32 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) acc[i][j] += xv[i] * yv[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) CoreAcc<T>::add(run_s[i][j], run_c[i][j], acc[i][j]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int xi = tx0 + ty + 8 * i, p = tp0 + tx + 32 * j;
+      if (xi < a.nX && p < a.P)
+        a.part[((size_t)ks * a.nX + xi) * a.P + p] = CoreAcc<T>::value(run_s[i][j], run_c[i][j]);
+    }
+}
+
+// Packed M of block (s0 + sidx, q chunk) in FP64 from the split partials.
+__global__ void core_gram_merge_kernel(const double* __restrict__ part, int ksplit, int nX, int P, int J0, int mq,
+                                       int nY, int sidx, double* __restrict__ gram) {
+  const int b = J0 * mq, nm = b * (b + 1) / 2;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nm; e += gridDim.x * blockDim.x) {
+    int k, l;
+    entry_kl(e, b, k, l);
+    const int xi = sym_index(k % J0, l % J0, J0);
+    const int p = sidx * nY + sym_index(k / J0, l / J0, mq);
+    double s = 0.0;
+    for (int c = 0; c < ksplit; ++c) s += part[((size_t)c * nX + xi) * P + p];
+    gram[e] = s;
+  }
+}
+
+// ================================================================== g pass (one block)
+struct GPassArgs {
+  int J0, J1;
+  CoreBlock cur, prev;
+  int has_prev;
+  const double* dprev;
+  int64_t nnz, ntasks;
+  double* part;  // [ctas][b]
+};
+
+template <typename T>
+struct HTerm {
+  const T* sR;
+  const T* sW;
+  int m;
+  __device__ TermPtrs<T> prep(int p) const { return TermPtrs<T>{sR, sW + p, 1, m}; }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kCoreTask) core_g_pass_kernel(DevModel<T> M, DevMode<T> csr, T* r, GPassArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int J0 = a.J0, m = a.cur.m, b = a.cur.b;
+  const int mp = a.has_prev ? a.prev.m : 0;
+  size_t off = 0;
+  int64_t* sptr = reinterpret_cast<int64_t*>(smem_raw + off); off += (size_t)(kCoreTask + 2) * 8;
+  double* sdp = reinterpret_cast<double*>(smem_raw + off); off += (size_t)kCoreMaxB * 8;
+  T* sA0 = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * J0 * sizeof(T);
+  T* sU = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * kCoreMaxM * sizeof(T);
+  T* sW = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * m * sizeof(T);
+  T* sR = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  T* sH = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreKmax * m * sizeof(T);
+  T* sPart = reinterpret_cast<T*>(smem_raw + off);
+  __shared__ PieceScratch pscr;
+  if (a.has_prev)
+    for (int i = threadIdx.x; i < a.prev.b; i += blockDim.x) sdp[i] = a.dprev[i];
+  // thread t < b owns g entry (j0 = t % J0, q = t / J0)
+  const int own = (int)threadIdx.x < b;
+  const int oj = own ? (int)threadIdx.x % J0 : 0, oq = own ? (int)threadIdx.x / J0 : 0;
+  T gs = T(0), gc = T(0);
+  const int R = *csr.nnzrows;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  __syncthreads();
+  for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
+    const int64_t t0 = task * kCoreTask, t1 = min(t0 + (int64_t)kCoreTask, a.nnz);
+    const int cnt = (int)(t1 - t0);
+    int64_t k0;
+    const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, sptr, &k0);
+    // per piece: a0 row and u(q) = sum_j0 Delta_prev(j0, q) a0[j0]
     for (int k = warp; k < nrows; k += nwarps) {
       const int64_t row = csr.nzrow[k0 + k];
       for (int j = lane; j < J0; j += 32) sA0[k * J0 + j] = M.A[0][row * J0 + j];
@@ -187,107 +347,61 @@ __global__ void __launch_bounds__(kCoreTask) core_pass_kernel(DevModel<T> M, Dev
       for (int q = lane; q < mp; q += 32) {
         T u = T(0);
         for (int j = 0; j < J0; ++j) u += (T)sdp[q * J0 + j] * sA0[k * J0 + j];
-        sU[k * mp + q] = u;
+        sU[k * kCoreMaxM + q] = u;
       }
     }
     __syncthreads();
-    // phase 1: per entry, apply the previous block to r, form w
     if ((int)threadIdx.x < cnt) {
       const int64_t p = t0 + threadIdx.x;
       const int lr = local_row(sptr, nrows, p);
-      const int64_t i1 = csr.oidx[p];
-      const T* a1 = M.A[1] + i1 * a.J1;
-      T r = r_in[p];
+      const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * a.J1;
+      T rv = r[p];
       if (a.has_prev) {
-        const T cp = suffix_weight<T>(M, csr.oidx, a.nnz, p, a.prev.s);
-        T acc2 = T(0);
-        for (int q = 0; q < mp; ++q) acc2 += sU[lr * mp + q] * a1[a.prev.q0 + q];
-        r -= cp * acc2;
-        r_out[p] = r;
+        T cp;
+        suffix_weights<T>(M, csr.oidx, a.nnz, p, a.prev.s, 1, &cp, 1);
+        T acc = T(0);
+        for (int q = 0; q < mp; ++q) acc += sU[lr * kCoreMaxM + q] * a1[a.prev.q0 + q];
+        rv -= cp * acc;
+        r[p] = rv;
       }
-      const T c = suffix_weight<T>(M, csr.oidx, a.nnz, p, a.cur.s);
+      T c;
+      suffix_weights<T>(M, csr.oidx, a.nnz, p, a.cur.s, 1, &c, 1);
       for (int q = 0; q < m; ++q) sW[threadIdx.x * m + q] = a1[a.cur.q0 + q] * c;
-      sR[threadIdx.x] = r;
+      sR[threadIdx.x] = rv;
     }
     __syncthreads();
-    // phase 2: per row piece Q (packed upper) and h
-    {
-      CoreTerm<T> f{sW, sR, m};
-      piece_sums<T>(sptr, nrows, t0, t1, QP, sQ, sPart, &pscr, f);
+    const HTerm<T> f{sR, sW, m};
+    T tacc = T(0);
+    for (int r0 = 0; r0 < nrows; r0 += kCoreKmax) {
+      const int nr = min(kCoreKmax, nrows - r0);
+      piece_sums<T>(sptr + r0, nr, t0, t1, m, sH, sPart, &pscr, f);
+      if (own)
+        for (int kr = 0; kr < nr; ++kr) tacc += sA0[(r0 + kr) * J0 + oj] * sH[kr * m + oq];
+      __syncthreads();
     }
-    // phase 3: Z += X (x) Y and g += a0 (x) h over the task's pieces (storage type),
-    // then into the block's running sums (Kahan for FP32)
-#pragma unroll
-    for (int i = 0; i < kCoreEPT; ++i) tacc[i] = T(0);
-    for (int k = 0; k < nrows; ++k) {
-      const T* a0 = sA0 + k * J0;
-      const T* Q = sQ + k * QP;
-#pragma unroll
-      for (int i = 0; i < kCoreEPT; ++i) {
-        if (i >= nown) continue;
-        const uint32_t c = code[i];
-        const int ia = (int)(c & 255u), ib = (int)((c >> 8) & 255u), iq = (int)(c >> 16);
-        const T xa = ib == 255 ? a0[ia] : a0[ia] * a0[ib];
-        tacc[i] += xa * Q[iq];
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < kCoreEPT; ++i)
-      if (i < nown) {
-        const int e = threadIdx.x + i * blockDim.x;
-        CoreAcc<T>::add(sSum[e], sComp[e], tacc[i]);
-      }
-    __syncthreads();
+    if (own) CoreAcc<T>::add(gs, gc, tacc);
   }
-#pragma unroll
-  for (int i = 0; i < kCoreEPT; ++i)
-    if (i < nown) {
-      const int e = threadIdx.x + i * blockDim.x;
-      a.part[(size_t)blockIdx.x * a.nz + e] = CoreAcc<T>::value(sSum[e], sComp[e]);
-    }
+  if (own) a.part[(size_t)blockIdx.x * b + threadIdx.x] = CoreAcc<T>::value(gs, gc);
 }
 
-__device__ __forceinline__ int sym_index(int x, int y, int n) {
-  const int lo = min(x, y), hi = max(x, y);
-  return lo * n - (lo * (lo - 1)) / 2 + (hi - lo);
-}
-
-// Fixed-order FP64 sum of the per-block partials, expanded from the Kronecker
-// form into the packed block Gram M (k <= l) followed by g.
-__global__ void core_merge_kernel(const double* __restrict__ part, int nctas, int nz, int nent, int b, int J0, int m,
-                                  double* __restrict__ tot) {
-  const int nm = b * (b + 1) / 2, nY = m * (m + 1) / 2, nX = J0 * (J0 + 1) / 2;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nent; e += gridDim.x * blockDim.x) {
-    int z;
-    if (e < nm) {
-      int k, l;
-      entry_kl(e, b, k, l);
-      z = sym_index(k % J0, l % J0, J0) * nY + sym_index(k / J0, l / J0, m);
-    } else {
-      const int k = e - nm;
-      z = nX * nY + (k % J0) + J0 * (k / J0);
-    }
+__global__ void core_vec_merge_kernel(const double* __restrict__ part, int nctas, int n, double* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int c = 0; c < nctas; ++c) s += part[(size_t)c * nz + z];
-    tot[e] = s;
+    for (int c = 0; c < nctas; ++c) s += part[(size_t)c * n + e];
+    out[e] = s;
   }
 }
-
 
 // Exact sequential updates of one block (Eq. 12 / Eq. 14), one thread block.
 template <typename T>
 __global__ void core_solve_kernel(DevModel<T> M, CoreBlock blk, int J0, int J1, int reg, double lambda,
-                                  const double* __restrict__ tot, double* __restrict__ dout) {
+                                  const double* __restrict__ gram, const double* __restrict__ g,
+                                  double* __restrict__ dout) {
   __shared__ double grad[kCoreMaxB];
   __shared__ double dk_s;
   const int b = blk.b;
-  const int nm = b * (b + 1) / 2;
-  for (int k = threadIdx.x; k < b; k += blockDim.x) grad[k] = tot[nm + k];
+  for (int k = threadIdx.x; k < b; k += blockDim.x) grad[k] = g[k];
   __syncthreads();
-  auto Mkl = [&](int k, int l) {
-    const int lo = min(k, l), hi = max(k, l);
-    return tot[lo * b - (lo * (lo - 1)) / 2 + (hi - lo)];
-  };
   for (int k = 0; k < b; ++k) {
     const int j0 = k % J0, q = k / J0;
     const int64_t lin = (int64_t)j0 + (int64_t)J0 * (blk.q0 + q) + (int64_t)J0 * J1 * blk.s;
@@ -295,12 +409,12 @@ __global__ void core_solve_kernel(DevModel<T> M, CoreBlock blk, int J0, int J1, 
       double dk = 0.0;
       if (!M.Gmask[lin]) {
         const double gold = (double)M.G[lin];
-        const double mkk = Mkl(k, k);
+        const double mkk = gram[sym_index(k, k, b)];
         const double num = grad[k] + gold * mkk;
         double nv;
         if (reg == VEST_REG_L1) {
-          const double gc = -2.0 * num, dc = 2.0 * mkk;
-          nv = gc > lambda ? (lambda - gc) / dc : (gc < -lambda ? -(lambda + gc) / dc : 0.0);
+          const double gcv = -2.0 * num, dc = 2.0 * mkk;
+          nv = gcv > lambda ? (lambda - gcv) / dc : (gcv < -lambda ? -(lambda + gcv) / dc : 0.0);
         } else {
           nv = num / (lambda + mkk);
         }
@@ -314,139 +428,377 @@ __global__ void core_solve_kernel(DevModel<T> M, CoreBlock blk, int J0, int J1, 
     __syncthreads();
     const double dk = dk_s;
     if (dk != 0.0)
-      for (int l = k + 1 + threadIdx.x; l < b; l += blockDim.x) grad[l] -= dk * Mkl(k, l);
+      for (int l = k + 1 + threadIdx.x; l < b; l += blockDim.x) grad[l] -= dk * gram[sym_index(k, l, b)];
     __syncthreads();
   }
 }
 
-// Responsibility of the block's core elements from g (sum r P) and diag(M) (sum P^2).
+// ================================================================== stats pass (responsibility)
+// For a group of suffixes [s0, s0 + Sg) and every j_1: per piece sum r w and sum w^2
+// with w = a1[j_1] c(s); then S1(j0, j1, s) += a0[j0] sum r w, S2 += a0[j0]^2 sum w^2.
+struct StatsArgs {
+  int J0, J1;
+  int64_t s0;
+  int Sg, SJ, P, kmax;
+  int64_t nnz, ntasks;
+  double* part;  // [ctas][2 * J0 * SJ]
+};
+
 template <typename T>
-__global__ void core_resp_kernel(DevModel<T> M, CoreBlock blk, int J0, int J1, const double* __restrict__ tot,
+struct StatsTerm {
+  const T* sR;
+  const T* sW;
+  int SJ;
+  __device__ TermPtrs<T> prep(int p) const {
+    if (p < SJ) return TermPtrs<T>{sR, sW + p, 1, SJ};
+    return TermPtrs<T>{sW + (p - SJ), sW + (p - SJ), SJ, SJ};
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kCoreTask) core_stats_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ r,
+                                                               StatsArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int J0 = a.J0, SJ = a.SJ, P = a.P;
+  size_t off = 0;
+  int64_t* sptr = reinterpret_cast<int64_t*>(smem_raw + off); off += (size_t)(kCoreTask + 2) * 8;
+  T* sA0 = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * J0 * sizeof(T);
+  T* sW = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * SJ * sizeof(T);
+  T* sR = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  T* sAcc = reinterpret_cast<T*>(smem_raw + off); off += (size_t)a.kmax * P * sizeof(T);
+  T* sPart = reinterpret_cast<T*>(smem_raw + off);
+  __shared__ PieceScratch pscr;
+  const int nacc = 2 * J0 * SJ;
+  T rs[kStatsEPT], rc[kStatsEPT], tacc[kStatsEPT];
+#pragma unroll
+  for (int i = 0; i < kStatsEPT; ++i) rs[i] = rc[i] = T(0);
+  const int R = *csr.nnzrows;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
+    const int64_t t0 = task * kCoreTask, t1 = min(t0 + (int64_t)kCoreTask, a.nnz);
+    const int cnt = (int)(t1 - t0);
+    int64_t k0;
+    const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, sptr, &k0);
+    for (int k = warp; k < nrows; k += nwarps) {
+      const int64_t row = csr.nzrow[k0 + k];
+      for (int j = lane; j < J0; j += 32) sA0[k * J0 + j] = M.A[0][row * J0 + j];
+    }
+    if ((int)threadIdx.x < cnt) {
+      const int64_t p = t0 + threadIdx.x;
+      const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * a.J1;
+      T* w = sW + threadIdx.x * SJ;
+      suffix_weights<T>(M, csr.oidx, a.nnz, p, a.s0, a.Sg, w, a.J1);  // c(s) at w[s * J1]
+      for (int si = 0; si < a.Sg; ++si) {
+        const T c = w[si * a.J1];
+        for (int q = 0; q < a.J1; ++q) w[si * a.J1 + q] = a1[q] * c;
+      }
+      sR[threadIdx.x] = r[p];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kStatsEPT; ++i) tacc[i] = T(0);
+    const StatsTerm<T> f{sR, sW, SJ};
+    for (int r0 = 0; r0 < nrows; r0 += a.kmax) {
+      const int nr = min(a.kmax, nrows - r0);
+      piece_sums<T>(sptr + r0, nr, t0, t1, P, sAcc, sPart, &pscr, f);
+#pragma unroll
+      for (int i = 0; i < kStatsEPT; ++i) {
+        const int e = threadIdx.x + i * blockDim.x;
+        if (e >= nacc) continue;
+        const int kind = e / (J0 * SJ), rem = e % (J0 * SJ);
+        const int j0 = rem % J0, sq = rem / J0;
+        for (int kr = 0; kr < nr; ++kr) {
+          const T av = sA0[(r0 + kr) * J0 + j0];
+          tacc[i] += kind == 0 ? av * sAcc[kr * P + sq] : av * av * sAcc[kr * P + SJ + sq];
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < kStatsEPT; ++i) CoreAcc<T>::add(rs[i], rc[i], tacc[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < kStatsEPT; ++i) {
+    const int e = threadIdx.x + i * blockDim.x;
+    if (e < nacc) a.part[(size_t)blockIdx.x * nacc + e] = CoreAcc<T>::value(rs[i], rc[i]);
+  }
+}
+
+// Delta and Resp of the group's core elements: lin = j0 + J0 (j1 + J1 s).
+template <typename T>
+__global__ void core_resp_kernel(DevModel<T> M, int J0, int J1, int64_t s0, int SJ, const double* __restrict__ sums,
                                  const double* __restrict__ stats, double* __restrict__ delta, double* __restrict__ resp) {
-  const int b = blk.b, nm = b * (b + 1) / 2;
   const double xx = stats[1], re = stats[4];
-  for (int k = threadIdx.x; k < b; k += blockDim.x) {
-    const int j0 = k % J0, q = k / J0;
-    const int64_t lin = (int64_t)j0 + (int64_t)J0 * (blk.q0 + q) + (int64_t)J0 * J1 * blk.s;
+  const int n = J0 * SJ;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int64_t lin = (int64_t)J0 * J1 * s0 + e;  // e = j0 + J0 * (j1 + J1 * si)
     const double gv = (double)M.G[lin];
-    const double mkk = tot[k * b - (k * (k - 1)) / 2];
-    const double dl = 2.0 * gv * tot[nm + k] + gv * gv * mkk;
+    const double dl = 2.0 * gv * sums[e] + gv * gv * sums[n + e];
     delta[lin] = dl;
     if (resp) resp[lin] = re > 0.0 ? (sqrt(fmax(re * re + dl / xx, 0.0)) - re) / re : 0.0;
   }
 }
 
 // ------------------------------------------------------------------ host side
-// m = j_1 values per block: b = J_0 * m <= 128, and m <= 10 so the per-piece
-// Q buffers (m(m+1)/2 + m values per row piece) fit in shared memory.
-static void plan_blocks(const int32_t* J, int N, int* m_out, int64_t* nsuffix) {
-  const int J0 = J[0], J1 = J[1];
-  int m = std::max(1, kCoreMaxB / J0);
-  m = std::min(std::min(m, J1), kCoreMaxM);
-  *m_out = m;
-  int64_t S = 1;
-  for (int n = 2; n < N; ++n) S *= J[n];
-  *nsuffix = S;
+struct CorePlan {
+  int J0, J1, m, nq0;
+  int64_t S;       // suffixes
+  int64_t nblocks;
+  int bmax, nmmax;
+  int nX, nYmax, SgMax, Pmax;  // gram groups
+  int SgStats, SJ;             // stats groups
+  int64_t slots;
+};
+
+static CorePlan core_plan(const int32_t* J, int N, int64_t nnz, int64_t cap0) {
+  CorePlan c{};
+  c.J0 = J[0];
+  c.J1 = J[1];
+  c.m = std::min(std::min(std::max(1, kCoreMaxB / c.J0), c.J1), kCoreMaxM);
+  c.nq0 = (c.J1 + c.m - 1) / c.m;
+  c.S = 1;
+  for (int n = 2; n < N; ++n) c.S *= J[n];
+  c.nblocks = c.S * c.nq0;
+  c.bmax = c.J0 * c.m;
+  c.nmmax = c.bmax * (c.bmax + 1) / 2;
+  c.nX = c.J0 * (c.J0 + 1) / 2;
+  c.nYmax = c.m * (c.m + 1) / 2;
+  c.SgMax = (int)std::max<int64_t>(1, std::min<int64_t>(c.S, kGramMaxP / c.nYmax));
+  c.Pmax = 0;
+  for (int q0 = 0; q0 < c.J1; q0 += c.m) {  // the last j_1 chunk may be narrower and take more suffixes
+    const int mq = std::min(c.m, c.J1 - q0), nY = mq * (mq + 1) / 2;
+    const int sg = (int)std::max<int64_t>(1, std::min<int64_t>(c.S, kGramMaxP / nY));
+    c.Pmax = std::max(c.Pmax, sg * nY);
+  }
+  // stats: 2 * SJ outputs per piece <= 512, 2 * J0 * SJ accumulators <= kStatsEPT * 256
+  int sg = (int)std::max<int64_t>(1, std::min<int64_t>(c.S, 256 / c.J1));
+  while (sg > 1 && 2 * c.J0 * sg * c.J1 > kStatsEPT * kCoreTask) --sg;
+  c.SgStats = sg;
+  c.SJ = sg * c.J1;
+  c.slots = cap0 + ceil_div(std::max<int64_t>(nnz, 1), kCoreTask) + 1;
+  return c;
 }
 
-size_t core_part_bytes(const vest_model* m) {
-  int mm;
-  int64_t S;
-  plan_blocks(m->ranks, m->order, &mm, &S);
-  const int J0 = m->ranks[0];
-  return (size_t)kCorePassCtas * (size_t)((J0 * (J0 + 1) / 2) * (mm * (mm + 1) / 2) + J0 * mm) * 8;
+size_t core_scratch_bytes(const vest_model* m, int64_t nnz, int64_t cap0, size_t* y_bytes, size_t* gram_bytes,
+                          size_t* part_bytes) {
+  const CorePlan c = core_plan(m->ranks, m->order, nnz, cap0);
+  const size_t sT = m->dtype == VEST_F64 ? 8 : 4;
+  *y_bytes = align_up((size_t)c.slots * c.Pmax * sT) + align_up((size_t)c.slots * 4);
+  // the gram region also holds the responsibility sums (2 * J0 * SJ doubles)
+  *gram_bytes = align_up(std::max((size_t)c.nblocks * c.nmmax, (size_t)2 * c.J0 * c.SJ) * 8);
+  const size_t gemm = (size_t)kGramKSplit * c.nX * c.Pmax * 8;
+  const size_t gp = (size_t)kCorePassCtas * kCoreMaxB * 8;
+  const size_t st = (size_t)kCorePassCtas * 2 * c.J0 * c.SJ * 8;
+  *part_bytes = align_up(std::max({gemm, gp, st}));
+  return *y_bytes + *gram_bytes + *part_bytes;
 }
 
 template <typename T>
-static size_t pass_smem(int J0, int m, int mp, int nz) {
-  const int QP = m * (m + 1) / 2 + m;
-  size_t off = (size_t)(kCoreTask + 2) * 8 + (size_t)kCoreMaxB * 8;
-  off += (size_t)kCoreTask * J0 * sizeof(T);
-  off += (size_t)kCoreTask * std::max(mp, 1) * sizeof(T);
-  off += (size_t)kCoreTask * m * sizeof(T);
-  off += (size_t)kCoreTask * sizeof(T);
-  off += (size_t)kCoreTask * QP * sizeof(T);
-  off += (size_t)kMaxLongPieces * QP * sizeof(T);
-  off += 2 * (size_t)nz * sizeof(T);
-  return off;
+static size_t smem_gram(int nY, int Sg, int P, int kmax) {
+  size_t off = (size_t)(kCoreTask + 2) * 8 + (size_t)kCoreTask * nY * sizeof(T) + (size_t)kCoreTask * Sg * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  return off + (size_t)kmax * P * sizeof(T) + (size_t)kMaxLongPieces * P * sizeof(T);
 }
 
-// Runs the block passes; with solve = true this is the core sweep, otherwise it
-// collects the responsibility statistics of every core element.
 template <typename T>
-static vest_status core_blocks(const vest_index* ix, const vest_model* mdl, int reg, double lambda, bool solve,
-                               T* r0, const double* stats, double* delta_core, double* resp_core, char* scratch,
-                               const ScratchPlan& plan, cudaStream_t s) {
-  const DevModel<T> M = dev_model<T>(mdl);
-  if (M.N < 2) return fail(VEST_ERR_UNSUPPORTED, "order < 2");
-  int m;
-  int64_t S;
-  plan_blocks(M.J, M.N, &m, &S);
+static size_t smem_gpass(int J0, int m) {
+  size_t off = (size_t)(kCoreTask + 2) * 8 + (size_t)kCoreMaxB * 8 + (size_t)kCoreTask * J0 * sizeof(T) +
+               (size_t)kCoreTask * kCoreMaxM * sizeof(T) + (size_t)kCoreTask * m * sizeof(T) + (size_t)kCoreTask * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  return off + (size_t)kCoreKmax * m * sizeof(T) + (size_t)kMaxLongPieces * m * sizeof(T);
+}
+
+template <typename T>
+static size_t smem_stats(int J0, int SJ, int P, int kmax) {
+  size_t off = (size_t)(kCoreTask + 2) * 8 + (size_t)kCoreTask * J0 * sizeof(T) + (size_t)kCoreTask * SJ * sizeof(T) +
+               (size_t)kCoreTask * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  return off + (size_t)kmax * P * sizeof(T) + (size_t)kMaxLongPieces * P * sizeof(T);
+}
+
+template <typename T>
+static int kmax_for(int P) {
+  return (int)std::max<size_t>(1, std::min<size_t>(kCoreKmax, (48 * 1024) / ((size_t)P * sizeof(T))));
+}
+
+template <typename T>
+static vest_status set_smem(void (*kern)(DevModel<T>, DevMode<T>, T*, GPassArgs), size_t smem) {
+  VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return VEST_OK;
+}
+
+struct CoreBufs {
+  void* Y;
+  int32_t* srow;
+  double* gram;
+  double* part;
+  double* small;
+};
+
+static CoreBufs core_bufs(const vest_index* ix, const vest_model* m, char* scratch, const ScratchPlan& plan) {
+  const CorePlan c = core_plan(m->ranks, m->order, ix->nnz, ix->mode[0].cap);
+  const size_t sT = m->dtype == VEST_F64 ? 8 : 4;
+  CoreBufs b;
+  char* base = scratch + plan.off_core;
+  b.Y = base;
+  b.srow = reinterpret_cast<int32_t*>(base + align_up((size_t)c.slots * c.Pmax * sT));
+  size_t yb, gb, pb;
+  core_scratch_bytes(m, ix->nnz, ix->mode[0].cap, &yb, &gb, &pb);
+  b.gram = reinterpret_cast<double*>(base + yb);
+  b.part = reinterpret_cast<double*>(base + yb + gb);
+  b.small = reinterpret_cast<double*>(scratch + plan.off_small);
+  return b;
+}
+
+// All block Grams, packed, block bi at gram + bi * nmmax.
+template <typename T>
+static vest_status core_grams(const vest_index* ix, const DevModel<T>& M, const CorePlan& c, const CoreBufs& bf,
+                              cudaStream_t s) {
   const DevMode<T> csr = dev_mode<T>(ix, 0);
-  CoreArgs a{};
-  a.N = M.N;
-  a.J0 = M.J[0];
-  a.J1 = M.J[1];
-  a.nnz = ix->nnz;
-  a.ntasks = ceil_div(ix->nnz, kCoreTask);
-  a.part = reinterpret_cast<double*>(scratch + plan.off_part);
-  double* small = reinterpret_cast<double*>(scratch + plan.off_small);
-  double* tot = small;                       // [<= 128*129/2 + 128]
-  double* dbuf[2] = {small + 9000, small + 9000 + kCoreMaxB};
-  const int nctas = (int)std::max<int64_t>(1, std::min<int64_t>(a.ntasks, kCorePassCtas));
-  int iblk = 0;
-  for (int64_t sfx = 0; sfx < S; ++sfx) {
-    for (int q0 = 0; q0 < a.J1; q0 += m) {
-      CoreBlock blk{sfx, q0, std::min(m, a.J1 - q0), 0};
-      blk.b = a.J0 * blk.m;
-      a.cur = blk;
-      a.nent = blk.b * (blk.b + 1) / 2 + blk.b;
-      a.nz = (a.J0 * (a.J0 + 1) / 2) * (blk.m * (blk.m + 1) / 2) + a.J0 * blk.m;
-      if ((size_t)nctas * a.nz * 8 > plan.part_bytes) return fail(VEST_ERR_WORKSPACE, "core partial region too small");
-      if (a.nz > kCoreEPT * kCoreTask) return fail(VEST_ERR_UNSUPPORTED, "core block too large");
-      a.has_prev = (solve && iblk > 0) ? 1 : 0;
-      a.dprev = dbuf[(iblk + 1) & 1];
+  const int64_t ntasks = ceil_div(ix->nnz, kCoreTask);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntasks, (int64_t)num_sms() * 4));
+  for (int qc = 0; qc < c.nq0; ++qc) {
+    const int q0 = qc * c.m, mq = std::min(c.m, c.J1 - q0), nY = mq * (mq + 1) / 2;
+    const int Sg = (int)std::max<int64_t>(1, std::min<int64_t>(c.S, kGramMaxP / nY));
+    for (int64_t s0 = 0; s0 < c.S; s0 += Sg) {
+      const int sg = (int)std::min<int64_t>(Sg, c.S - s0);
+      GramArgs ga{};
+      ga.J0 = c.J0;
+      ga.J1 = c.J1;
+      ga.q0 = q0;
+      ga.mq = mq;
+      ga.nY = nY;
+      ga.s0 = s0;
+      ga.Sg = sg;
+      ga.P = sg * nY;
+      ga.kmax = kmax_for<T>(ga.P);
+      ga.nnz = ix->nnz;
+      ga.ntasks = ntasks;
+      ga.Y = bf.Y;
+      ga.srow = bf.srow;
+      VEST_CUDA(cudaMemsetAsync(bf.srow, 0xFF, (size_t)c.slots * 4, s));
       if (ix->nnz > 0) {
-        const size_t smem = pass_smem<T>(a.J0, blk.m, a.has_prev ? a.prev.m : 0, a.nz);
-        auto kern = core_pass_kernel<T>;
+        const size_t smem = smem_gram<T>(nY, sg, ga.P, ga.kmax);
+        auto kern = core_gram_pass_kernel<T>;
         VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<nctas, kCoreTask, smem, s>>>(M, csr, r0, r0, a);
-        VEST_LAUNCH("core_pass_kernel");
-        core_merge_kernel<<<(unsigned)ceil_div(a.nent, 256), 256, 0, s>>>(a.part, nctas, a.nz, a.nent, blk.b, a.J0,
-                                                                          blk.m, tot);
-        VEST_LAUNCH("core_merge_kernel");
-      } else {
-        VEST_CUDA(cudaMemsetAsync(tot, 0, (size_t)a.nent * 8, s));
+        kern<<<grid, kCoreTask, smem, s>>>(M, csr, ga);
+        VEST_LAUNCH("core_gram_pass_kernel");
       }
-      if (solve) {
-        core_solve_kernel<T><<<1, 128, 0, s>>>(M, blk, a.J0, a.J1, reg, lambda, tot, dbuf[iblk & 1]);
-        VEST_LAUNCH("core_solve_kernel");
-      } else {
-        core_resp_kernel<T><<<1, 128, 0, s>>>(M, blk, a.J0, a.J1, tot, stats, delta_core, resp_core);
-        VEST_LAUNCH("core_resp_kernel");
+      GemmArgs gm{};
+      gm.J0 = c.J0;
+      gm.nX = c.nX;
+      gm.P = ga.P;
+      gm.nslots = c.slots;
+      gm.Y = bf.Y;
+      gm.srow = bf.srow;
+      gm.part = bf.part;
+      const dim3 gg((unsigned)(((c.nX + 31) / 32) * ((ga.P + 63) / 64)), kGramKSplit);
+      core_gram_gemm_kernel<T><<<gg, 256, 0, s>>>(M, csr, gm);
+      VEST_LAUNCH("core_gram_gemm_kernel");
+      const int b = c.J0 * mq, nm = b * (b + 1) / 2;
+      for (int si = 0; si < sg; ++si) {
+        const int64_t bi = (s0 + si) * c.nq0 + qc;
+        core_gram_merge_kernel<<<(unsigned)ceil_div(nm, 256), 256, 0, s>>>(bf.part, kGramKSplit, c.nX, ga.P, c.J0, mq,
+                                                                           nY, si, bf.gram + bi * c.nmmax);
+        VEST_LAUNCH("core_gram_merge_kernel");
       }
-      a.prev = blk;
-      ++iblk;
     }
   }
   return VEST_OK;
 }
 
 template <typename T>
-vest_status sweep_core_impl(const vest_index* ix, const vest_model* m, int reg, double lambda, char* scratch,
+vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg, double lambda, char* scratch,
                             const ScratchPlan& plan, cudaStream_t s) {
+  const DevModel<T> M = dev_model<T>(mdl);
+  if (M.N < 2) return fail(VEST_ERR_UNSUPPORTED, "order < 2");
+  const CorePlan c = core_plan(M.J, M.N, ix->nnz, ix->mode[0].cap);
+  const CoreBufs bf = core_bufs(ix, mdl, scratch, plan);
   T* r0 = reinterpret_cast<T*>(scratch + plan.off_resid);
-  double* out = reinterpret_cast<double*>(scratch + plan.off_small) + 9000 + 2 * kCoreMaxB;
-  VEST_TRY(loss_impl<T>(ix, m, reg, lambda, out, r0, nullptr, scratch, plan, s));
-  return core_blocks<T>(ix, m, reg, lambda, true, r0, nullptr, nullptr, nullptr, scratch, plan, s);
+  double* out = bf.small + 9000 + 3 * kCoreMaxB;
+  double* gvec = bf.small + 9000 + 2 * kCoreMaxB;
+  double* dbuf[2] = {bf.small + 9000, bf.small + 9000 + kCoreMaxB};
+  VEST_TRY(loss_impl<T>(ix, mdl, reg, lambda, out, r0, nullptr, scratch, plan, s));
+  VEST_TRY(core_grams<T>(ix, M, c, bf, s));
+  const DevMode<T> csr = dev_mode<T>(ix, 0);
+  const int64_t ntasks = ceil_div(ix->nnz, kCoreTask);
+  const int nctas = (int)std::max<int64_t>(1, std::min<int64_t>(ntasks, kCorePassCtas));
+  GPassArgs a{};
+  a.J0 = c.J0;
+  a.J1 = c.J1;
+  a.nnz = ix->nnz;
+  a.ntasks = ntasks;
+  a.part = bf.part;
+  int64_t iblk = 0;
+  for (int64_t sfx = 0; sfx < c.S; ++sfx) {
+    for (int qc = 0; qc < c.nq0; ++qc, ++iblk) {
+      const int q0 = qc * c.m;
+      CoreBlock blk{sfx, q0, std::min(c.m, c.J1 - q0), 0};
+      blk.b = c.J0 * blk.m;
+      a.cur = blk;
+      a.has_prev = iblk > 0;
+      a.dprev = dbuf[(iblk + 1) & 1];
+      if (ix->nnz > 0) {
+        const size_t smem = smem_gpass<T>(c.J0, blk.m);
+        VEST_TRY(set_smem<T>(core_g_pass_kernel<T>, smem));
+        core_g_pass_kernel<T><<<nctas, kCoreTask, smem, s>>>(M, csr, r0, a);
+        VEST_LAUNCH("core_g_pass_kernel");
+        core_vec_merge_kernel<<<1, 128, 0, s>>>(bf.part, nctas, blk.b, gvec);
+        VEST_LAUNCH("core_vec_merge_kernel");
+      } else {
+        VEST_CUDA(cudaMemsetAsync(gvec, 0, (size_t)blk.b * 8, s));
+      }
+      core_solve_kernel<T><<<1, 128, 0, s>>>(M, blk, c.J0, c.J1, reg, lambda, bf.gram + iblk * c.nmmax, gvec,
+                                             dbuf[iblk & 1]);
+      VEST_LAUNCH("core_solve_kernel");
+      a.prev = blk;
+    }
+  }
+  return VEST_OK;
 }
 
 template <typename T>
-vest_status core_responsibility(const vest_index* ix, const vest_model* m, const T* resid_csr0, const double* stats,
+vest_status core_responsibility(const vest_index* ix, const vest_model* mdl, const T* resid_csr0, const double* stats,
                                 double* delta_core, double* resp_core, char* scratch, const ScratchPlan& plan,
                                 cudaStream_t s) {
-  return core_blocks<T>(ix, m, 0, 0.0, false, const_cast<T*>(resid_csr0), stats, delta_core, resp_core, scratch,
-                        plan, s);
+  const DevModel<T> M = dev_model<T>(mdl);
+  if (M.N < 2) return fail(VEST_ERR_UNSUPPORTED, "order < 2");
+  const CorePlan c = core_plan(M.J, M.N, ix->nnz, ix->mode[0].cap);
+  const CoreBufs bf = core_bufs(ix, mdl, scratch, plan);
+  const DevMode<T> csr = dev_mode<T>(ix, 0);
+  const int64_t ntasks = ceil_div(ix->nnz, kCoreTask);
+  const int nctas = (int)std::max<int64_t>(1, std::min<int64_t>(ntasks, kCorePassCtas));
+  double* sums = bf.gram;  // reuse the gram region: [2 * J0 * SJ]
+  for (int64_t s0 = 0; s0 < c.S; s0 += c.SgStats) {
+    StatsArgs a{};
+    a.J0 = c.J0;
+    a.J1 = c.J1;
+    a.s0 = s0;
+    a.Sg = (int)std::min<int64_t>(c.SgStats, c.S - s0);
+    a.SJ = a.Sg * c.J1;
+    a.P = 2 * a.SJ;
+    a.kmax = kmax_for<T>(a.P);
+    a.nnz = ix->nnz;
+    a.ntasks = ntasks;
+    a.part = bf.part;
+    const int nacc = 2 * c.J0 * a.SJ;
+    if (ix->nnz > 0) {
+      const size_t smem = smem_stats<T>(c.J0, a.SJ, a.P, a.kmax);
+      auto kern = core_stats_kernel<T>;
+      VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<nctas, kCoreTask, smem, s>>>(M, csr, resid_csr0, a);
+      VEST_LAUNCH("core_stats_kernel");
+      core_vec_merge_kernel<<<(unsigned)ceil_div(nacc, 256), 256, 0, s>>>(bf.part, nctas, nacc, sums);
+      VEST_LAUNCH("core_vec_merge_kernel");
+    } else {
+      VEST_CUDA(cudaMemsetAsync(sums, 0, (size_t)nacc * 8, s));
+    }
+    core_resp_kernel<T><<<(unsigned)ceil_div(c.J0 * a.SJ, 256), 256, 0, s>>>(M, c.J0, c.J1, s0, a.SJ, sums, stats,
+                                                                              delta_core, resp_core);
+    VEST_LAUNCH("core_resp_kernel");
+  }
+  return VEST_OK;
 }
 
 template vest_status sweep_core_impl<float>(const vest_index*, const vest_model*, int, double, char*,
