@@ -33,7 +33,7 @@ constexpr int kCoreMaxB = 128;
 constexpr int kCoreMaxM = 10;
 constexpr int kGramMaxP = 576;      // per-piece gram outputs per group
 constexpr int kGramKSplit = 64;     // fixed: reduction order does not depend on the device
-constexpr int kCorePassCtas = 296;  // fixed likewise
+constexpr int kCorePassCtas = 1216;  // fixed likewise (8 per SM on 152 SMs)
 constexpr int kStatsEPT = 16;       // stats accumulators per thread
 constexpr int kCoreKmax = 64;       // row pieces per phase-2 round
 
@@ -285,9 +285,14 @@ __global__ void core_gram_merge_kernel(const double* __restrict__ part, int kspl
     entry_kl(e, b, k, l);
     const int xi = sym_index(k % J0, l % J0, J0);
     const int p = sidx * nY + sym_index(k / J0, l / J0, mq);
-    double s = 0.0;
-    for (int c = 0; c < ksplit; ++c) s += part[((size_t)c * nX + xi) * P + p];
-    gram[e] = s;
+    double c4[4] = {0, 0, 0, 0};
+    int c = 0;
+    for (; c + 3 < ksplit; c += 4) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) c4[k] += part[((size_t)(c + k) * nX + xi) * P + p];
+    }
+    for (; c < ksplit; ++c) c4[0] += part[((size_t)c * nX + xi) * P + p];
+    gram[e] = (c4[0] + c4[1]) + (c4[2] + c4[3]);
   }
 }
 
@@ -384,52 +389,79 @@ __global__ void __launch_bounds__(kCoreTask) core_g_pass_kernel(DevModel<T> M, D
   if (own) a.part[(size_t)blockIdx.x * b + threadIdx.x] = CoreAcc<T>::value(gs, gc);
 }
 
+// out[e] = sum over c of part[c][e] in FP64: block of 8 warps x 32 outputs, warp w
+// sums c = w, w + 8, ... with four independent chains, warps combined in order.
 __global__ void core_vec_merge_kernel(const double* __restrict__ part, int nctas, int n, double* __restrict__ out) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+  __shared__ double sh[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  double c4[4] = {0, 0, 0, 0};
+  if (e < n) {
+    int c = w, u = 0;
+    for (; c + 24 < nctas; c += 32) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) c4[k] += part[(size_t)(c + 8 * k) * n + e];
+    }
+    for (; c < nctas; c += 8, ++u) c4[u & 3] += part[(size_t)c * n + e];
+  }
+  sh[w][lane] = (c4[0] + c4[1]) + (c4[2] + c4[3]);
+  __syncthreads();
+  if (w == 0 && e < n) {
     double s = 0.0;
-    for (int c = 0; c < nctas; ++c) s += part[(size_t)c * n + e];
+    for (int k = 0; k < 8; ++k) s += sh[k][lane];
     out[e] = s;
   }
 }
 
-// Exact sequential updates of one block (Eq. 12 / Eq. 14), one thread block.
+// Exact sequential updates of one block (Eq. 12 / Eq. 14) by one warp: lane
+// k % 32 holds the running sum_alpha r P(k) of element k; after each update
+// every lane subtracts Delta_k M_kl from the elements l > k it holds.
 template <typename T>
 __global__ void core_solve_kernel(DevModel<T> M, CoreBlock blk, int J0, int J1, int reg, double lambda,
                                   const double* __restrict__ gram, const double* __restrict__ g,
                                   double* __restrict__ dout) {
-  __shared__ double grad[kCoreMaxB];
-  __shared__ double dk_s;
+  constexpr int kPer = kCoreMaxB / 32;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
   const int b = blk.b;
-  for (int k = threadIdx.x; k < b; k += blockDim.x) grad[k] = g[k];
-  __syncthreads();
+  double grad[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int l = lane + 32 * i;
+    grad[i] = l < b ? g[l] : 0.0;
+  }
   for (int k = 0; k < b; ++k) {
     const int j0 = k % J0, q = k / J0;
     const int64_t lin = (int64_t)j0 + (int64_t)J0 * (blk.q0 + q) + (int64_t)J0 * J1 * blk.s;
-    if (threadIdx.x == 0) {
-      double dk = 0.0;
-      if (!M.Gmask[lin]) {
-        const double gold = (double)M.G[lin];
-        const double mkk = gram[sym_index(k, k, b)];
-        const double num = grad[k] + gold * mkk;
-        double nv;
-        if (reg == VEST_REG_L1) {
-          const double gcv = -2.0 * num, dc = 2.0 * mkk;
-          nv = gcv > lambda ? (lambda - gcv) / dc : (gcv < -lambda ? -(lambda + gcv) / dc : 0.0);
-        } else {
-          nv = num / (lambda + mkk);
-        }
-        const T st = (T)nv;
-        M.G[lin] = st;
-        dk = (double)st - gold;
+    double gk = 0.0;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i)
+      if (k / 32 == i) gk = grad[i];
+    gk = __shfl_sync(0xffffffffu, gk, k & 31);
+    double dk = 0.0;
+    if (!M.Gmask[lin]) {
+      const double gold = (double)M.G[lin];
+      const double mkk = gram[sym_index(k, k, b)];
+      const double num = gk + gold * mkk;
+      double nv;
+      if (reg == VEST_REG_L1) {
+        const double gcv = -2.0 * num, dc = 2.0 * mkk;
+        nv = gcv > lambda ? (lambda - gcv) / dc : (gcv < -lambda ? -(lambda + gcv) / dc : 0.0);
+      } else {
+        nv = num / (lambda + mkk);
       }
-      dk_s = dk;
-      dout[k] = dk;
+      const T st = (T)nv;
+      dk = (double)st - gold;
+      if (lane == 0) M.G[lin] = st;
     }
-    __syncthreads();
-    const double dk = dk_s;
-    if (dk != 0.0)
-      for (int l = k + 1 + threadIdx.x; l < b; l += blockDim.x) grad[l] -= dk * gram[sym_index(k, l, b)];
-    __syncthreads();
+    if (lane == 0) dout[k] = dk;
+    if (dk != 0.0) {
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int l = lane + 32 * i;
+        if (l > k && l < b) grad[i] -= dk * gram[sym_index(k, l, b)];
+      }
+    }
   }
 }
 
@@ -744,12 +776,12 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
         VEST_TRY(set_smem<T>(core_g_pass_kernel<T>, smem));
         core_g_pass_kernel<T><<<nctas, kCoreTask, smem, s>>>(M, csr, r0, a);
         VEST_LAUNCH("core_g_pass_kernel");
-        core_vec_merge_kernel<<<1, 128, 0, s>>>(bf.part, nctas, blk.b, gvec);
+        core_vec_merge_kernel<<<(unsigned)ceil_div(blk.b, 32), 256, 0, s>>>(bf.part, nctas, blk.b, gvec);
         VEST_LAUNCH("core_vec_merge_kernel");
       } else {
         VEST_CUDA(cudaMemsetAsync(gvec, 0, (size_t)blk.b * 8, s));
       }
-      core_solve_kernel<T><<<1, 128, 0, s>>>(M, blk, c.J0, c.J1, reg, lambda, bf.gram + iblk * c.nmmax, gvec,
+      core_solve_kernel<T><<<1, 32, 0, s>>>(M, blk, c.J0, c.J1, reg, lambda, bf.gram + iblk * c.nmmax, gvec,
                                              dbuf[iblk & 1]);
       VEST_LAUNCH("core_solve_kernel");
       a.prev = blk;
@@ -789,7 +821,7 @@ vest_status core_responsibility(const vest_index* ix, const vest_model* mdl, con
       VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       kern<<<nctas, kCoreTask, smem, s>>>(M, csr, resid_csr0, a);
       VEST_LAUNCH("core_stats_kernel");
-      core_vec_merge_kernel<<<(unsigned)ceil_div(nacc, 256), 256, 0, s>>>(bf.part, nctas, nacc, sums);
+      core_vec_merge_kernel<<<(unsigned)ceil_div(nacc, 32), 256, 0, s>>>(bf.part, nctas, nacc, sums);
       VEST_LAUNCH("core_vec_merge_kernel");
     } else {
       VEST_CUDA(cudaMemsetAsync(sums, 0, (size_t)nacc * 8, s));

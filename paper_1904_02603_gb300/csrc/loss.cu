@@ -13,7 +13,7 @@
 namespace vest {
 
 constexpr int kLossTask = 256;
-constexpr int kLossCtas = 592;
+constexpr int kLossCtas = 1216;
 constexpr int kRegCtas = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -44,7 +44,8 @@ struct LossArgs {
   double* part;  // [ctas][2]
 };
 
-template <typename T, int JN, int NSLOW>
+// E entries per thread (threadIdx.x + e * blockDim.x of each 256-entry task).
+template <typename T, int JN, int JF, int NSLOW, int E>
 __global__ void __launch_bounds__(kLossTask) loss_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ gcore,
                                                          LossArgs a, T* __restrict__ resid_csr0,
                                                          T* __restrict__ resid_coo) {
@@ -68,27 +69,37 @@ __global__ void __launch_bounds__(kLossTask) loss_kernel(DevModel<T> M, DevMode<
   __syncthreads();
   for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
     const int64_t t0 = task * kLossTask, t1 = min(t0 + (int64_t)kLossTask, nnz);
+    const int cnt = (int)(t1 - t0);
     int64_t k0;
     const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, sptr, &k0);
-    const int64_t p = t0 + threadIdx.x;
-    if (p < t1) {
-      const int lr = local_row(sptr, nrows, p);
-      const int64_t i0 = csr.nzrow[k0 + lr];
-      SlowRows sr;
-      const T* rowf = gather_rows<T, NSLOW>(M, r, csr.oidx, nnz, p, sr);
-      T d[JN];
-      compute_delta<T, JN, NSLOW>(d, g, a.onz, r.n_outer, r.Jf, rowf, sr, r.nslow);
-      const T* a0 = M.A[0] + i0 * J0;
-      T b = T(0);
+    if ((int)threadIdx.x < cnt) {
+      const T* rowf[E];
+      SlowRows sr[E];
 #pragma unroll
-      for (int j = 0; j < JN; ++j)
-        if (j < J0) b += __ldg(a0 + j) * d[j];
-      const T x = csr.val[p];
-      const T res = x - b;
-      if (resid_csr0) resid_csr0[p] = res;
-      if (resid_coo) resid_coo[csr.perm[p]] = res;
-      sq += (double)res * (double)res;
-      xx += (double)x * (double)x;
+      for (int e = 0; e < E; ++e) {
+        const int q = threadIdx.x + e * blockDim.x;
+        rowf[e] = gather_rows<T, NSLOW>(M, r, csr.oidx, nnz, t0 + (q < cnt ? q : (int)threadIdx.x), sr[e]);
+      }
+      T d[E][JN];
+      compute_delta_multi<T, JN, JF, NSLOW, E>(d, g, a.onz, r.n_outer, r.Jf, rowf, sr, r.nslow);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int q = threadIdx.x + e * blockDim.x;
+        if (q >= cnt) continue;
+        const int64_t p = t0 + q;
+        const int64_t i0 = csr.nzrow[k0 + local_row(sptr, nrows, p)];
+        const T* a0 = M.A[0] + i0 * J0;
+        T b = T(0);
+#pragma unroll
+        for (int j = 0; j < JN; ++j)
+          if (j < J0) b += __ldg(a0 + j) * d[e][j];
+        const T x = csr.val[p];
+        const T res = x - b;
+        if (resid_csr0) resid_csr0[p] = res;
+        if (resid_coo) resid_coo[csr.perm[p]] = res;
+        sq += (double)res * (double)res;
+        xx += (double)x * (double)x;
+      }
     }
     __syncthreads();
   }
@@ -140,22 +151,30 @@ __global__ void loss_final_kernel(const double* __restrict__ lpart, int nl, cons
 
 constexpr size_t kLossSmemBudget = 160 * 1024;
 
-template <typename T, int JN, int NSLOW>
+template <typename T, int JN, int JF, int NSLOW, int E>
 static vest_status launch_loss(const DevModel<T>& M, const DevMode<T>& csr, const T* gp, const LossArgs& a,
                                size_t smem, int grid, T* r0, T* rc, cudaStream_t s) {
-  auto kern = loss_kernel<T, JN, NSLOW>;
+  auto kern = loss_kernel<T, JN, JF, NSLOW, E>;
   VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, kLossTask, smem, s>>>(M, csr, gp, a, r0, rc);
+  kern<<<grid, kLossTask / E, smem, s>>>(M, csr, gp, a, r0, rc);
   VEST_LAUNCH("loss_kernel");
   return VEST_OK;
 }
 
+// FP32: two entries per thread, f-mode rows in registers when the rank equals the bucket width.
 template <typename T, int JN>
-static vest_status loss_nslow(int nslow, const DevModel<T>& M, const DevMode<T>& csr, const T* gp, const LossArgs& a,
-                              size_t smem, int grid, T* r0, T* rc, cudaStream_t s) {
-  if (nslow == 1) return launch_loss<T, JN, 1>(M, csr, gp, a, smem, grid, r0, rc, s);
-  if (nslow == 2) return launch_loss<T, JN, 2>(M, csr, gp, a, smem, grid, r0, rc, s);
-  return launch_loss<T, JN, -1>(M, csr, gp, a, smem, grid, r0, rc, s);
+static vest_status loss_nslow(int nslow, int Jf, const DevModel<T>& M, const DevMode<T>& csr, const T* gp,
+                              const LossArgs& a, size_t smem, int grid, T* r0, T* rc, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (nslow == 1 && Jf == JN) return launch_loss<T, JN, JN, 1, 2>(M, csr, gp, a, smem, grid, r0, rc, s);
+    if (nslow == 1) return launch_loss<T, JN, 0, 1, 2>(M, csr, gp, a, smem, grid, r0, rc, s);
+    if (nslow == 2 && Jf == JN) return launch_loss<T, JN, JN, 2, 2>(M, csr, gp, a, smem, grid, r0, rc, s);
+    if (nslow == 2) return launch_loss<T, JN, 0, 2, 2>(M, csr, gp, a, smem, grid, r0, rc, s);
+  } else {
+    if (nslow == 1) return launch_loss<T, JN, 0, 1, 1>(M, csr, gp, a, smem, grid, r0, rc, s);
+    if (nslow == 2) return launch_loss<T, JN, 0, 2, 1>(M, csr, gp, a, smem, grid, r0, rc, s);
+  }
+  return launch_loss<T, JN, 0, -1, 1>(M, csr, gp, a, smem, grid, r0, rc, s);
 }
 
 template <typename T>
@@ -185,12 +204,12 @@ vest_status loss_impl(const vest_index* ix, const vest_model* m, int reg, double
   if (ix->nnz > 0) {
     const DevMode<T> csr = dev_mode<T>(ix, 0);
     switch (JN) {
-      case 4: VEST_TRY((loss_nslow<T, 4>(r.nslow, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
-      case 8: VEST_TRY((loss_nslow<T, 8>(r.nslow, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
-      case 10: VEST_TRY((loss_nslow<T, 10>(r.nslow, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
-      case 12: VEST_TRY((loss_nslow<T, 12>(r.nslow, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
-      case 16: VEST_TRY((loss_nslow<T, 16>(r.nslow, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
-      default: VEST_TRY((loss_nslow<T, 32>(r.nslow, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
+      case 4: VEST_TRY((loss_nslow<T, 4>(r.nslow, r.Jf, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
+      case 8: VEST_TRY((loss_nslow<T, 8>(r.nslow, r.Jf, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
+      case 10: VEST_TRY((loss_nslow<T, 10>(r.nslow, r.Jf, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
+      case 12: VEST_TRY((loss_nslow<T, 12>(r.nslow, r.Jf, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
+      case 16: VEST_TRY((loss_nslow<T, 16>(r.nslow, r.Jf, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
+      default: VEST_TRY((loss_nslow<T, 32>(r.nslow, r.Jf, M, csr, gp, a, smem, grid, resid_csr0, resid_coo, s))); break;
     }
   }
   reg_kernel<T><<<kRegCtas, 256, 0, s>>>(M, reg, rpart);

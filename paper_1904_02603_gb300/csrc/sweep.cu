@@ -231,11 +231,18 @@ __global__ void __launch_bounds__(256) sweep_fixup_kernel(DevModel<T> M, DevMode
     const int pstep = groups > 1 ? P : (int)blockDim.x;
     if (gi < groups) {
       for (int pp = pstart; pp < P; pp += pstep) {
+        // the first task's piece, then eight independent chains over the rest (fixed order)
         double acc = 0.0;
-        for (int64_t tt = task + gi; tt <= tlast; tt += groups) {
-          const int slot = (tt == task) ? first_slot : 0;
-          acc += a.spill[((size_t)tt * 2 + slot) * P + pp];
+        if (task + gi <= tlast) acc = a.spill[((size_t)(task + gi) * 2 + (gi == 0 ? first_slot : 0)) * P + pp];
+        double c8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int64_t tt = task + gi + groups;
+        for (; tt + 7 * groups <= tlast; tt += 8 * groups) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) c8[u] += a.spill[((size_t)(tt + u * groups) * 2) * P + pp];
         }
+        for (int u = 0; tt <= tlast; tt += groups, ++u) c8[u & 7] += a.spill[((size_t)tt * 2) * P + pp];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += c8[u];
         part[gi * P + pp] = acc;
       }
     }
