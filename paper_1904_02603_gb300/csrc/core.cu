@@ -301,92 +301,115 @@ struct GPassArgs {
   int J0, J1;
   CoreBlock cur, prev;
   int has_prev;
-  const double* dprev;
-  int64_t nnz, ntasks;
+  int64_t nnz;
   double* part;  // [ctas][b]
 };
 
+// u(k, q) = sum_j0 Delta_prev(j0, q) a0[row_k, j0] for every non-empty mode-0 row k.
 template <typename T>
-struct HTerm {
-  const T* sR;
-  const T* sW;
-  int m;
-  __device__ TermPtrs<T> prep(int p) const { return TermPtrs<T>{sR, sW + p, 1, m}; }
-};
-
-template <typename T>
-__global__ void __launch_bounds__(kCoreTask) core_g_pass_kernel(DevModel<T> M, DevMode<T> csr, T* r, GPassArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int J0 = a.J0, m = a.cur.m, b = a.cur.b;
-  const int mp = a.has_prev ? a.prev.m : 0;
-  size_t off = 0;
-  int64_t* sptr = reinterpret_cast<int64_t*>(smem_raw + off); off += (size_t)(kCoreTask + 2) * 8;
-  double* sdp = reinterpret_cast<double*>(smem_raw + off); off += (size_t)kCoreMaxB * 8;
-  T* sA0 = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * J0 * sizeof(T);
-  T* sU = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * kCoreMaxM * sizeof(T);
-  T* sW = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * m * sizeof(T);
-  T* sR = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * sizeof(T);
-  off = (off + 15) & ~(size_t)15;
-  T* sH = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreKmax * m * sizeof(T);
-  T* sPart = reinterpret_cast<T*>(smem_raw + off);
-  __shared__ PieceScratch pscr;
-  if (a.has_prev)
-    for (int i = threadIdx.x; i < a.prev.b; i += blockDim.x) sdp[i] = a.dprev[i];
-  // thread t < b owns g entry (j0 = t % J0, q = t / J0)
-  const int own = (int)threadIdx.x < b;
-  const int oj = own ? (int)threadIdx.x % J0 : 0, oq = own ? (int)threadIdx.x / J0 : 0;
-  T gs = T(0), gc = T(0);
-  const int R = *csr.nnzrows;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+__global__ void core_u_kernel(DevModel<T> M, const int32_t* __restrict__ nzrow, const int32_t* __restrict__ nnzrows,
+                              const double* __restrict__ dprev, int J0, int mp, T* __restrict__ U) {
+  __shared__ double sd[kCoreMaxB];
+  for (int i = threadIdx.x; i < J0 * mp; i += blockDim.x) sd[i] = dprev[i];
   __syncthreads();
-  for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
-    const int64_t t0 = task * kCoreTask, t1 = min(t0 + (int64_t)kCoreTask, a.nnz);
-    const int cnt = (int)(t1 - t0);
-    int64_t k0;
-    const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, sptr, &k0);
-    // per piece: a0 row and u(q) = sum_j0 Delta_prev(j0, q) a0[j0]
-    for (int k = warp; k < nrows; k += nwarps) {
-      const int64_t row = csr.nzrow[k0 + k];
-      for (int j = lane; j < J0; j += 32) sA0[k * J0 + j] = M.A[0][row * J0 + j];
-      __syncwarp();
-      for (int q = lane; q < mp; q += 32) {
-        T u = T(0);
-        for (int j = 0; j < J0; ++j) u += (T)sdp[q * J0 + j] * sA0[k * J0 + j];
-        sU[k * kCoreMaxM + q] = u;
-      }
+  const int64_t R = *nnzrows;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < R; k += (int64_t)gridDim.x * blockDim.x) {
+    const T* a0 = M.A[0] + (int64_t)nzrow[k] * J0;
+    for (int q = 0; q < mp; ++q) {
+      T u = T(0);
+      for (int j = 0; j < J0; ++j) u += (T)sd[q * J0 + j] * a0[j];
+      U[k * kCoreMaxM + q] = u;
     }
-    __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      const int64_t p = t0 + threadIdx.x;
-      const int lr = local_row(sptr, nrows, p);
+  }
+}
+
+// One streaming pass per block.  Each warp takes 32 consecutive entries at a
+// time: it applies the previous block's Delta to r (r -= c' a1 . u(row)), forms
+// h(q) = r a1[q0 + q] c, adds h over each row segment inside the warp, and every
+// segment head adds a0[row] (x) h into the warp's g accumulators (lane l holds
+// entries l, l + 32, ...; Kahan across heads).  g is linear in the rows, so row
+// segments cut by chunk edges need no fix-up.
+template <typename T>
+__global__ void __launch_bounds__(256) core_g_pass_kernel(DevModel<T> M, DevMode<T> csr, T* r, const T* __restrict__ U,
+                                                          GPassArgs a) {
+  constexpr int kPer = kCoreMaxB / 32;
+  __shared__ T sh[8][kCoreMaxM];
+  __shared__ double sw[8][kCoreMaxB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int J0 = a.J0, m = a.cur.m, b = a.cur.b, mp = a.has_prev ? a.prev.m : 0;
+  T as[kPer], ac[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) as[i] = ac[i] = T(0);
+  const int64_t nchunks = ceil_div(a.nnz, 32);
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp, nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t ch = gw; ch < nchunks; ch += nw) {
+    const int64_t p = ch * 32 + lane;
+    const bool valid = p < a.nnz;
+    const int k = valid ? csr.rowk[p] : -1 - lane;
+    T h[kCoreMaxM];
+#pragma unroll
+    for (int q = 0; q < kCoreMaxM; ++q) h[q] = T(0);
+    if (valid) {
       const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * a.J1;
       T rv = r[p];
       if (a.has_prev) {
         T cp;
         suffix_weights<T>(M, csr.oidx, a.nnz, p, a.prev.s, 1, &cp, 1);
+        const T* u = U + (int64_t)k * kCoreMaxM;
         T acc = T(0);
-        for (int q = 0; q < mp; ++q) acc += sU[lr * kCoreMaxM + q] * a1[a.prev.q0 + q];
+#pragma unroll
+        for (int q = 0; q < kCoreMaxM; ++q)
+          if (q < mp) acc += a1[a.prev.q0 + q] * u[q];
         rv -= cp * acc;
         r[p] = rv;
       }
       T c;
       suffix_weights<T>(M, csr.oidx, a.nnz, p, a.cur.s, 1, &c, 1);
-      for (int q = 0; q < m; ++q) sW[threadIdx.x * m + q] = a1[a.cur.q0 + q] * c;
-      sR[threadIdx.x] = rv;
+      const T rc = rv * c;
+#pragma unroll
+      for (int q = 0; q < kCoreMaxM; ++q)
+        if (q < m) h[q] = rc * a1[a.cur.q0 + q];
     }
-    __syncthreads();
-    const HTerm<T> f{sR, sW, m};
-    T tacc = T(0);
-    for (int r0 = 0; r0 < nrows; r0 += kCoreKmax) {
-      const int nr = min(kCoreKmax, nrows - r0);
-      piece_sums<T>(sptr + r0, nr, t0, t1, m, sH, sPart, &pscr, f);
-      if (own)
-        for (int kr = 0; kr < nr; ++kr) tacc += sA0[(r0 + kr) * J0 + oj] * sH[kr * m + oq];
-      __syncthreads();
+    // segmented suffix sums: lane l ends with the sum over its row from l to the chunk end
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int ko = __shfl_down_sync(0xffffffffu, k, o);
+#pragma unroll
+      for (int q = 0; q < kCoreMaxM; ++q) {
+        const T v = __shfl_down_sync(0xffffffffu, h[q], o);
+        if (lane + o < 32 && ko == k) h[q] += v;
+      }
     }
-    if (own) CoreAcc<T>::add(gs, gc, tacc);
+    const int kup = __shfl_up_sync(0xffffffffu, k, 1);
+    unsigned heads = __ballot_sync(0xffffffffu, valid && (lane == 0 || kup != k));
+    while (heads) {
+      const int hl = __ffs(heads) - 1;
+      heads &= heads - 1;
+      const int kk = __shfl_sync(0xffffffffu, k, hl);
+      if (lane == hl) {
+#pragma unroll
+        for (int q = 0; q < kCoreMaxM; ++q)
+          if (q < m) sh[warp][q] = h[q];
+      }
+      __syncwarp();
+      const T* a0 = M.A[0] + (int64_t)csr.nzrow[kk] * J0;
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int e = lane + 32 * i;
+        if (e < b) CoreAcc<T>::add(as[i], ac[i], a0[e % J0] * sh[warp][e / J0]);
+      }
+      __syncwarp();
+    }
   }
-  if (own) a.part[(size_t)blockIdx.x * b + threadIdx.x] = CoreAcc<T>::value(gs, gc);
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) sw[warp][lane + 32 * i] = CoreAcc<T>::value(as[i], ac[i]);
+  __syncthreads();
+  const int nwarps = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < b; e += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < nwarps; ++w) t += sw[w][e];
+    a.part[(size_t)blockIdx.x * b + e] = t;
+  }
 }
 
 // out[e] = sum over c of part[c][e] in FP64: block of 8 warps x 32 outputs, warp w
@@ -418,12 +441,15 @@ __global__ void core_vec_merge_kernel(const double* __restrict__ part, int nctas
 // every lane subtracts Delta_k M_kl from the elements l > k it holds.
 template <typename T>
 __global__ void core_solve_kernel(DevModel<T> M, CoreBlock blk, int J0, int J1, int reg, double lambda,
-                                  const double* __restrict__ gram, const double* __restrict__ g,
-                                  double* __restrict__ dout) {
+                                  const double* gram, const double* __restrict__ g, double* __restrict__ dout) {
   constexpr int kPer = kCoreMaxB / 32;
+  extern __shared__ double sgram[];
   const int lane = threadIdx.x & 31;
-  if (threadIdx.x >= 32) return;
   const int b = blk.b;
+  for (int e = threadIdx.x; e < b * (b + 1) / 2; e += blockDim.x) sgram[e] = gram[e];
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  gram = sgram;
   double grad[kPer];
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
@@ -616,7 +642,9 @@ size_t core_scratch_bytes(const vest_model* m, int64_t nnz, int64_t cap0, size_t
                           size_t* part_bytes) {
   const CorePlan c = core_plan(m->ranks, m->order, nnz, cap0);
   const size_t sT = m->dtype == VEST_F64 ? 8 : 4;
-  *y_bytes = align_up((size_t)c.slots * c.Pmax * sT) + align_up((size_t)c.slots * 4);
+  // per-piece gram statistics, later reused for u per non-empty mode-0 row (cap0 x kCoreMaxM)
+  *y_bytes = align_up(std::max((size_t)c.slots * c.Pmax, (size_t)(cap0 + 1) * kCoreMaxM) * sT) +
+             align_up((size_t)c.slots * 4);
   // the gram region also holds the responsibility sums (2 * J0 * SJ doubles)
   *gram_bytes = align_up(std::max((size_t)c.nblocks * c.nmmax, (size_t)2 * c.J0 * c.SJ) * 8);
   const size_t gemm = (size_t)kGramKSplit * c.nX * c.Pmax * 8;
@@ -634,14 +662,6 @@ static size_t smem_gram(int nY, int Sg, int P, int kmax) {
 }
 
 template <typename T>
-static size_t smem_gpass(int J0, int m) {
-  size_t off = (size_t)(kCoreTask + 2) * 8 + (size_t)kCoreMaxB * 8 + (size_t)kCoreTask * J0 * sizeof(T) +
-               (size_t)kCoreTask * kCoreMaxM * sizeof(T) + (size_t)kCoreTask * m * sizeof(T) + (size_t)kCoreTask * sizeof(T);
-  off = (off + 15) & ~(size_t)15;
-  return off + (size_t)kCoreKmax * m * sizeof(T) + (size_t)kMaxLongPieces * m * sizeof(T);
-}
-
-template <typename T>
 static size_t smem_stats(int J0, int SJ, int P, int kmax) {
   size_t off = (size_t)(kCoreTask + 2) * 8 + (size_t)kCoreTask * J0 * sizeof(T) + (size_t)kCoreTask * SJ * sizeof(T) +
                (size_t)kCoreTask * sizeof(T);
@@ -652,12 +672,6 @@ static size_t smem_stats(int J0, int SJ, int P, int kmax) {
 template <typename T>
 static int kmax_for(int P) {
   return (int)std::max<size_t>(1, std::min<size_t>(kCoreKmax, (48 * 1024) / ((size_t)P * sizeof(T))));
-}
-
-template <typename T>
-static vest_status set_smem(void (*kern)(DevModel<T>, DevMode<T>, T*, GPassArgs), size_t smem) {
-  VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  return VEST_OK;
 }
 
 struct CoreBufs {
@@ -674,7 +688,8 @@ static CoreBufs core_bufs(const vest_index* ix, const vest_model* m, char* scrat
   CoreBufs b;
   char* base = scratch + plan.off_core;
   b.Y = base;
-  b.srow = reinterpret_cast<int32_t*>(base + align_up((size_t)c.slots * c.Pmax * sT));
+  b.srow = reinterpret_cast<int32_t*>(
+      base + align_up(std::max((size_t)c.slots * c.Pmax, (size_t)(ix->mode[0].cap + 1) * kCoreMaxM) * sT));
   size_t yb, gb, pb;
   core_scratch_bytes(m, ix->nnz, ix->mode[0].cap, &yb, &gb, &pb);
   b.gram = reinterpret_cast<double*>(base + yb);
@@ -754,14 +769,13 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
   VEST_TRY(loss_impl<T>(ix, mdl, reg, lambda, out, r0, nullptr, scratch, plan, s));
   VEST_TRY(core_grams<T>(ix, M, c, bf, s));
   const DevMode<T> csr = dev_mode<T>(ix, 0);
-  const int64_t ntasks = ceil_div(ix->nnz, kCoreTask);
-  const int nctas = (int)std::max<int64_t>(1, std::min<int64_t>(ntasks, kCorePassCtas));
   GPassArgs a{};
   a.J0 = c.J0;
   a.J1 = c.J1;
   a.nnz = ix->nnz;
-  a.ntasks = ntasks;
   a.part = bf.part;
+  T* U = reinterpret_cast<T*>(bf.Y);  // the per-piece gram region is free again: u per row
+  const int nctas_g = kCorePassCtas;
   int64_t iblk = 0;
   for (int64_t sfx = 0; sfx < c.S; ++sfx) {
     for (int qc = 0; qc < c.nq0; ++qc, ++iblk) {
@@ -770,19 +784,23 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
       blk.b = c.J0 * blk.m;
       a.cur = blk;
       a.has_prev = iblk > 0;
-      a.dprev = dbuf[(iblk + 1) & 1];
       if (ix->nnz > 0) {
-        const size_t smem = smem_gpass<T>(c.J0, blk.m);
-        VEST_TRY(set_smem<T>(core_g_pass_kernel<T>, smem));
-        core_g_pass_kernel<T><<<nctas, kCoreTask, smem, s>>>(M, csr, r0, a);
+        if (a.has_prev) {
+          core_u_kernel<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->mode[0].cap, 256), num_sms() * 4)),
+                             256, 0, s>>>(M, csr.nzrow, csr.nnzrows, dbuf[(iblk + 1) & 1], c.J0, a.prev.m, U);
+          VEST_LAUNCH("core_u_kernel");
+        }
+        core_g_pass_kernel<T><<<nctas_g, 256, 0, s>>>(M, csr, r0, U, a);
         VEST_LAUNCH("core_g_pass_kernel");
-        core_vec_merge_kernel<<<(unsigned)ceil_div(blk.b, 32), 256, 0, s>>>(bf.part, nctas, blk.b, gvec);
+        core_vec_merge_kernel<<<(unsigned)ceil_div(blk.b, 32), 256, 0, s>>>(bf.part, nctas_g, blk.b, gvec);
         VEST_LAUNCH("core_vec_merge_kernel");
       } else {
         VEST_CUDA(cudaMemsetAsync(gvec, 0, (size_t)blk.b * 8, s));
       }
-      core_solve_kernel<T><<<1, 32, 0, s>>>(M, blk, c.J0, c.J1, reg, lambda, bf.gram + iblk * c.nmmax, gvec,
-                                             dbuf[iblk & 1]);
+      const size_t ssm = (size_t)(blk.b * (blk.b + 1) / 2) * 8;
+      auto sk = core_solve_kernel<T>;
+      VEST_CUDA(cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+      sk<<<1, 256, ssm, s>>>(M, blk, c.J0, c.J1, reg, lambda, bf.gram + iblk * c.nmmax, gvec, dbuf[iblk & 1]);
       VEST_LAUNCH("core_solve_kernel");
       a.prev = blk;
     }

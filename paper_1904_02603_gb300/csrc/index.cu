@@ -262,6 +262,13 @@ __global__ void row_start_flags_kernel(const uint32_t* __restrict__ skey, int64_
     flags[p] = (p == 0 || skey[p] != skey[p - 1]) ? 1 : 0;
 }
 
+// rowk[p] = number of row starts at or before p, minus one
+__global__ void rowk_kernel(const int32_t* __restrict__ flags, const int32_t* __restrict__ pos, int64_t n,
+                            int32_t* __restrict__ rowk) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    rowk[p] = pos[p] + flags[p] - 1;
+}
+
 __global__ void nzrows_kernel(const uint32_t* __restrict__ skey, int64_t n, const int32_t* __restrict__ flags,
                               const int32_t* __restrict__ pos, int64_t* __restrict__ nzptr, int32_t* __restrict__ nzrow,
                               int32_t* __restrict__ count) {
@@ -347,6 +354,7 @@ IndexLayout layout(const vest_tensor* t) {
     o += align_up((size_t)std::max<int64_t>(cap, 1) * 4);                          // nzrow
     o += align_up(4);                                                              // count
     o += align_up((size_t)(ceil_div(std::max<int64_t>(n, 1), 32) + 1) * 4);       // granule rows
+    o += align_up((size_t)std::max<int64_t>(n, 1) * 4);                           // row of every position
     L.mode_bytes[m] = o;
     off += o;
   }
@@ -426,7 +434,8 @@ vest_status build_index_impl(const vest_tensor* t, void* ws, size_t ws_bytes, ve
     mi.nzptr = reinterpret_cast<int64_t*>(mb + o); o += align_up((size_t)(cap + 1) * 8);
     mi.nzrow = reinterpret_cast<int32_t*>(mb + o); o += align_up((size_t)std::max<int64_t>(cap, 1) * 4);
     mi.nnzrows = reinterpret_cast<int32_t*>(mb + o); o += align_up(4);
-    mi.gran = reinterpret_cast<int32_t*>(mb + o);
+    mi.gran = reinterpret_cast<int32_t*>(mb + o); o += align_up((size_t)(ceil_div(std::max<int64_t>(n, 1), 32) + 1) * 4);
+    mi.rowk = reinterpret_cast<int32_t*>(mb + o);
     mi.cap = cap;
     if (n == 0) {
       VEST_CUDA(cudaMemsetAsync(mi.row_ptr, 0, (size_t)(t->dims[m] + 1) * 8, s));
@@ -451,6 +460,8 @@ vest_status build_index_impl(const vest_tensor* t, void* ws, size_t ws_bytes, ve
     VEST_TRY(exclusive_scan_i32(flags, pos, n, scan_tmp, s));
     nzrows_kernel<<<grid, 256, 0, s>>>(skey, n, flags, pos, mi.nzptr, mi.nzrow, mi.nnzrows);
     VEST_LAUNCH("nzrows");
+    rowk_kernel<<<grid, 256, 0, s>>>(flags, pos, n, mi.rowk);
+    VEST_LAUNCH("rowk");
     const int64_t ng = ceil_div(n, 32);
     granule_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ng, 256), num_sms() * 8)), 256, 0, s>>>(
         mi.nzptr, mi.nnzrows, ng, mi.gran);

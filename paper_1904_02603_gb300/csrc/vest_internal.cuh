@@ -54,6 +54,7 @@ struct ModeIndex {
   int32_t* nzrow;    // [cap]
   int32_t* nnzrows;  // device scalar R_n
   int32_t* gran;     // [ceil(nnz/32) + 1]: non-empty-row number k holding position 32 g
+  int32_t* rowk;     // [nnz]: non-empty-row number of every position
   int64_t cap;       // min(I_n, nnz)
 };
 
@@ -107,6 +108,7 @@ struct DevMode {
   const int32_t* nzrow;
   const int32_t* nnzrows;
   const int32_t* gran;
+  const int32_t* rowk;
   const int32_t* oidx;  // [(N-1)][nnz]
   const T* val;
   const int32_t* perm;
@@ -121,6 +123,7 @@ inline DevMode<T> dev_mode(const vest_index* ix, int n) {
   d.nzrow = mi.nzrow;
   d.nnzrows = mi.nnzrows;
   d.gran = mi.gran;
+  d.rowk = mi.rowk;
   d.oidx = mi.oidx;
   d.val = static_cast<const T*>(mi.val);
   d.perm = mi.perm;
