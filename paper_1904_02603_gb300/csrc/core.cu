@@ -450,23 +450,35 @@ __global__ void core_solve_kernel(DevModel<T> M, CoreBlock blk, int J0, int J1, 
   __syncthreads();
   if (threadIdx.x >= 32) return;
   gram = sgram;
-  double grad[kPer];
+  // lane holds, for its elements l = lane + 32 i: the running sum, the current value, the mask
+  double grad[kPer], gval[kPer];
+  int gmask[kPer];
+  auto lin_of = [&](int k) {
+    return (int64_t)(k % J0) + (int64_t)J0 * (blk.q0 + k / J0) + (int64_t)J0 * J1 * blk.s;
+  };
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
     const int l = lane + 32 * i;
     grad[i] = l < b ? g[l] : 0.0;
+    gval[i] = l < b ? (double)M.G[lin_of(l)] : 0.0;
+    gmask[i] = l < b ? (int)M.Gmask[lin_of(l)] : 1;
   }
   for (int k = 0; k < b; ++k) {
-    const int j0 = k % J0, q = k / J0;
-    const int64_t lin = (int64_t)j0 + (int64_t)J0 * (blk.q0 + q) + (int64_t)J0 * J1 * blk.s;
-    double gk = 0.0;
+    const int64_t lin = lin_of(k);
+    double gk = 0.0, gold = 0.0;
+    int mk = 1;
 #pragma unroll
     for (int i = 0; i < kPer; ++i)
-      if (k / 32 == i) gk = grad[i];
+      if (k / 32 == i) {
+        gk = grad[i];
+        gold = gval[i];
+        mk = gmask[i];
+      }
     gk = __shfl_sync(0xffffffffu, gk, k & 31);
+    gold = __shfl_sync(0xffffffffu, gold, k & 31);
+    mk = __shfl_sync(0xffffffffu, mk, k & 31);
     double dk = 0.0;
-    if (!M.Gmask[lin]) {
-      const double gold = (double)M.G[lin];
+    if (!mk) {
       const double mkk = gram[sym_index(k, k, b)];
       const double num = gk + gold * mkk;
       double nv;

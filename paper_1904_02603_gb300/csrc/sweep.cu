@@ -30,6 +30,7 @@ struct SweepArgs {
   int reg;
   double lambda;
   int64_t ntasks;
+  int64_t tpc;  // consecutive tasks per thread block
   int task;  // entries per task (blockDim * E)
   int kmax;  // row pieces per phase-2 round
   int P;
@@ -129,6 +130,9 @@ __global__ void __launch_bounds__(256) sweep_task_kernel(DevModel<T> M, DevMode<
   T* sPart = reinterpret_cast<T*>(smem_raw + off);
   off += (size_t)kMaxLongPieces * P * sizeof(T);
   int2* sTab = reinterpret_cast<int2*>(smem_raw + off);
+  off += (size_t)P * sizeof(int2);
+  off = (off + 15) & ~(size_t)15;
+  double* sCarry = reinterpret_cast<double*>(smem_raw + off);  // [2][P]: row sums carried to the next task
   __shared__ PieceScratch pscr;
 
   const T* g = gcore;
@@ -156,11 +160,16 @@ __global__ void __launch_bounds__(256) sweep_task_kernel(DevModel<T> M, DevMode<
   const int64_t nnz = csr.nnz;
   __syncthreads();
 
-  for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
+  // this block's consecutive tasks [tb, te) and the positions [rt0, rt1) they cover
+  const int64_t tb = blockIdx.x * a.tpc, te = min(tb + a.tpc, a.ntasks);
+  const int64_t rt0 = tb * TASK;
+  for (int64_t task = tb; task < te; ++task) {
     const int64_t t0 = task * TASK, t1 = min(t0 + (int64_t)TASK, nnz);
     const int cnt = (int)(t1 - t0);
     int64_t k0;
     const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, sptr, &k0);
+    double* cin = sCarry + (task & 1) * P;         // carried in from task - 1 (same block)
+    double* cout = sCarry + ((task + 1) & 1) * P;  // carried out to task + 1
 
     // phase 1: delta for the thread's E entries (threadIdx.x + e * blockDim.x)
     if ((int)threadIdx.x < cnt) {
@@ -193,54 +202,69 @@ __global__ void __launch_bounds__(256) sweep_task_kernel(DevModel<T> M, DevMode<
       const int nr = min(KMAX, nrows - r0);
       // phase 2: per-row sums over the task's pieces r0 .. r0 + nr - 1
       piece_sums<T>(sptr + r0, nr, t0, t1, P, sAcc, sPart, &pscr, f);
-      // phase 3: finish whole rows, spill cut ones
+      // phase 3: finish rows that end here; carry a row that continues into the
+      // block's next task; spill rows cut by the edges of the block's task range
       for (int kr = threadIdx.x; kr < nr; kr += blockDim.x) {
         const int k = r0 + kr;
         const int64_t rs = sptr[k], re = sptr[k + 1];
-        if (rs >= t0 && re <= t1) {
-          finish_row<T, T, MODE>(M, n, (int64_t)csr.nzrow[k0 + k], sAcc + kr * P, a);
+        const T* piece = sAcc + kr * P;
+        const bool carried_in = (k == 0) && rs < t0 && task > tb;  // earlier pieces are in cin
+        const bool continues = re > t1;
+        const bool started_here = rs >= rt0;
+        if (!continues && !carried_in && rs >= t0) {
+          finish_row<T, T, MODE>(M, n, (int64_t)csr.nzrow[k0 + k], piece, a);
         } else {
-          const int slot = (k == 0) ? 0 : 1;
-          double* sp = a.spill + ((size_t)task * 2 + slot) * P;
-          for (int i = 0; i < P; ++i) sp[i] = (double)sAcc[kr * P + i];
+          double* acc = continues ? cout : cin;
+          for (int i = 0; i < P; ++i) acc[i] = (double)piece[i] + (carried_in ? cin[i] : 0.0);
+          if (!continues) {
+            if (started_here) finish_row<T, double, MODE>(M, n, (int64_t)csr.nzrow[k0 + k], acc, a);
+            else {  // the row entered the block's range from an earlier block: incoming partial
+              double* sp = a.spill + ((size_t)blockIdx.x * 2 + 0) * P;
+              for (int i = 0; i < P; ++i) sp[i] = acc[i];
+            }
+          } else if (task + 1 == te) {  // leaves the block's range
+            double* sp = a.spill + ((size_t)blockIdx.x * 2 + (started_here ? 1 : 0)) * P;
+            for (int i = 0; i < P; ++i) sp[i] = acc[i];
+            a.spanning[blockIdx.x] = started_here ? (int32_t)(k0 + k) : -1;
+          }
         }
-        if (k == nrows - 1) a.spanning[task] = (rs >= t0 && re > t1) ? (int32_t)(k0 + k) : -1;
+        if (k == nrows - 1 && task + 1 == te && !(continues && started_here)) a.spanning[blockIdx.x] = -1;
       }
       __syncthreads();
     }
   }
 }
 
-// Rows cut by task edges: add the pieces in task order (FP64) and finish.
+// Rows cut by the edges of the blocks' task ranges: the block where the row starts
+// wrote its outgoing partial (slot 1), every later block the row reaches wrote
+// its incoming partial (slot 0); add them in block order (FP64) and finish.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) sweep_fixup_kernel(DevModel<T> M, DevMode<T> csr, SweepArgs a) {
+__global__ void __launch_bounds__(256) sweep_fixup_kernel(DevModel<T> M, DevMode<T> csr, SweepArgs a, int nblocks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* part = reinterpret_cast<double*>(smem_raw);  // [groups][P]
   const int P = a.P;
   const int groups = max(1, (int)blockDim.x / P);
-  for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
-    const int32_t kg = a.spanning[task];
+  for (int64_t c = blockIdx.x; c < nblocks; c += gridDim.x) {
+    const int32_t kg = a.spanning[c];
     if (kg < 0) continue;  // uniform across the block
-    const int64_t rs = csr.nzptr[kg], re = csr.nzptr[kg + 1];
-    const int64_t tlast = (re - 1) / a.task;
-    const int first_slot = (rs == task * (int64_t)a.task) ? 0 : 1;
-    // groups > 1: thread (gi, pi) sums output pi over tasks gi, gi + groups, ...;
-    // groups == 1 (P > blockDim): each thread sums outputs threadIdx.x + k * blockDim over all tasks
+    const int64_t re = csr.nzptr[kg + 1];
+    const int64_t clast = ((re - 1) / a.task) / a.tpc;
+    // groups > 1: thread (gi, pi) sums output pi over blocks c + gi, c + gi + groups, ...;
+    // groups == 1 (P > blockDim): each thread sums outputs threadIdx.x + k * blockDim over all blocks
     const int gi = groups > 1 ? (int)threadIdx.x / P : 0;
     const int pstart = groups > 1 ? (int)threadIdx.x % P : (int)threadIdx.x;
     const int pstep = groups > 1 ? P : (int)blockDim.x;
     if (gi < groups) {
       for (int pp = pstart; pp < P; pp += pstep) {
-        // the first task's piece, then eight independent chains over the rest (fixed order)
         double acc = 0.0;
-        if (task + gi <= tlast) acc = a.spill[((size_t)(task + gi) * 2 + (gi == 0 ? first_slot : 0)) * P + pp];
+        if (c + gi <= clast) acc = a.spill[((size_t)(c + gi) * 2 + (gi == 0 ? 1 : 0)) * P + pp];
         double c8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        int64_t tt = task + gi + groups;
-        for (; tt + 7 * groups <= tlast; tt += 8 * groups) {
+        int64_t cc = c + gi + groups;
+        for (; cc + 7 * groups <= clast; cc += 8 * groups) {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) c8[u] += a.spill[((size_t)(tt + u * groups) * 2) * P + pp];
+          for (int u = 0; u < 8; ++u) c8[u] += a.spill[((size_t)(cc + u * groups) * 2) * P + pp];
         }
-        for (int u = 0; tt <= tlast; tt += groups, ++u) c8[u & 7] += a.spill[((size_t)tt * 2) * P + pp];
+        for (int u = 0; cc <= clast; cc += groups, ++u) c8[u & 7] += a.spill[((size_t)cc * 2) * P + pp];
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc += c8[u];
         part[gi * P + pp] = acc;
@@ -285,6 +309,7 @@ static int outputs_per_row(int Jn, int mode_kind) {
 constexpr size_t kSmemBudget = 200 * 1024;
 constexpr size_t kAccBudget = 32 * 1024;
 constexpr int kTask = 256;
+constexpr int64_t kSweepBlocks = 2432;
 
 template <typename T>
 static int pieces_per_round(int P) {
@@ -301,6 +326,8 @@ static size_t task_smem(int task, int kmax, int JN, int P, size_t core_bytes) {
   off += (size_t)kmax * P * sizeof(T);
   off += (size_t)kMaxLongPieces * P * sizeof(T);
   off += (size_t)P * sizeof(int2);
+  off = (off + 15) & ~(size_t)15;
+  off += 2 * (size_t)P * sizeof(double);
   return off;
 }
 
@@ -320,8 +347,7 @@ static vest_status launch_task(const DevModel<T>& M, const DevMode<T>& csr, cons
                                size_t smem, cudaStream_t s) {
   auto kern = sweep_task_kernel<T, JN, JF, NSLOW, MODE, E>;
   VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int64_t grid = std::min<int64_t>(a.ntasks, (int64_t)num_sms() * 16);
-  kern<<<(unsigned)std::max<int64_t>(grid, 1), a.task / E, smem, s>>>(M, csr, gp, a);
+  kern<<<(unsigned)ceil_div(a.ntasks, a.tpc), a.task / E, smem, s>>>(M, csr, gp, a);
   VEST_LAUNCH("sweep_task_kernel");
   return VEST_OK;
 }
@@ -377,7 +403,11 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
   a.kmax = pieces_per_round<T>(a.P);
   a.use_smem_core = use_smem;
   a.ntasks = ceil_div(ix->nnz, a.task);
-  if ((size_t)a.ntasks * 2 * a.P * 8 > plan.spill_bytes || a.ntasks > plan.ntasks)
+  // a fixed number of thread blocks, each over consecutive tasks: the order of every
+  // sum is the same on any device
+  a.tpc = std::max<int64_t>(1, ceil_div(a.ntasks, kSweepBlocks));
+  const int64_t nblocks = std::max<int64_t>(1, ceil_div(a.ntasks, a.tpc));
+  if ((size_t)nblocks * 2 * a.P * 8 > plan.spill_bytes || nblocks > plan.ntasks)
     return fail(VEST_ERR_WORKSPACE, "scratch spill region too small");
   a.spill = reinterpret_cast<double*>(scratch + plan.off_spill);
   a.spanning = reinterpret_cast<int32_t*>(scratch + plan.off_spanning);
@@ -391,8 +421,8 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
   const size_t fsmem = (size_t)std::max(1, 256 / a.P) * a.P * 8 + 8 * a.P;
   auto fk = sweep_fixup_kernel<T, MODE>;
   VEST_CUDA(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
-  const int64_t fgrid = std::min<int64_t>(a.ntasks, (int64_t)num_sms() * 8);
-  fk<<<(unsigned)fgrid, 256, fsmem, s>>>(M, csr, a);
+  const int64_t fgrid = std::min<int64_t>(nblocks, (int64_t)num_sms() * 8);
+  fk<<<(unsigned)fgrid, 256, fsmem, s>>>(M, csr, a, (int)nblocks);
   VEST_LAUNCH("sweep_fixup_kernel");
   return VEST_OK;
 }
