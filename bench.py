@@ -18,6 +18,7 @@ instance of the workload (weak scaling, no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -171,6 +172,28 @@ def gpu_index_for_smi(local_rank: int) -> int:
     return local_rank
 
 
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the sweep task kernel from the committed ncu summary of this workload.
+
+    The summary records a hash of the kernel's sources; once they change the counters no longer
+    describe the kernel and the traffic is reported as null."""
+    path = os.path.join(ROOT, "profiles", f"sweep_task_kernel_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, "no ncu summary for this workload"
+    fields = dict(line.split(":", 1) for line in text.splitlines() if line.startswith(("source_sha256_16:",
+                                                                                          "dram_bytes_per_launch:")))
+    if len(fields) != 2:
+        return None, "ncu summary lacks source hash or traffic"
+    want = fields["source_sha256_16"].split("(")[0].split()
+    srcs = [os.path.join(ROOT, "paper_1904_02603_gb300", "csrc", f) for f in ("sweep.cu", "delta.cuh")]
+    have = [hashlib.sha256(open(f, "rb").read()).hexdigest()[:16] for f in srcs]
+    if want != have:
+        return None, "kernel sources changed since the ncu capture"
+    return float(fields["dram_bytes_per_launch"]), f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {path[len(ROOT) + 1:]}"
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -218,31 +241,34 @@ def main():
     units_per_step = N * nnz
 
     def step(model, index, evs=None):
+        # the factor sweep runs mode by mode (the same calls vest_sweep_factors(mode=-1) makes), so
+        # that each mode's sweep launch is timed on its own for the roofline
         if evs:
             evs[0].record(stream)
-        V.vest_sweep_factors(index, model, reg, w.lam, -1, sc)
-        if evs:
-            evs[1].record(stream)
+        for n in range(N):
+            V.vest_sweep_factors(index, model, reg, w.lam, n, sc)
+            if evs:
+                evs[1 + n].record(stream)
         V.vest_sweep_core(index, model, reg, w.lam, sc)
         if evs:
-            evs[2].record(stream)
+            evs[N + 1].record(stream)
         loss = V.vest_loss(index, model, reg, w.lam, sc)
         if evs:
-            evs[3].record(stream)
+            evs[N + 2].record(stream)
         df, dc, _, _ = V.vest_responsibility(index, model, sc, with_resp=False)
         if evs:
-            evs[4].record(stream)
+            evs[N + 3].record(stream)
         V.vest_prune(model, df, dc, 0.0, sc)
         if evs:
-            evs[5].record(stream)
+            evs[N + 4].record(stream)
         return loss
 
     for _ in range(args.warmup):
         step(mdl, ix)
     torch.cuda.synchronize()
 
-    ops = ["sweep_factors", "sweep_core", "loss", "responsibility", "prune"]
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    ops = [f"sweep_factors_mode{n}" for n in range(N)] + ["sweep_core", "loss", "responsibility", "prune"]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(ops) + 1)] for _ in range(args.steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(gpu_index_for_smi(local))
     time.sleep(0.5)
@@ -262,6 +288,8 @@ def main():
     elapsed_ms = start.elapsed_time(end)
     op_ms = {op: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
              for i, op in enumerate(ops)}
+    mode_ms = [op_ms[f"sweep_factors_mode{n}"] for n in range(N)]
+    op_ms["sweep_factors"] = sum(mode_ms)
     if world > 1:
         tt = torch.tensor([elapsed_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -302,31 +330,34 @@ def main():
             dist.destroy_process_group()
         return
 
-    # ---------------- roofline of the dominant kernel: the factor sweep
+    # ---------------- roofline of the dominant kernel: one mode's factor sweep (task kernel + fix-up)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = GB300_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     # algorithmic work per entry and mode (dense core): delta = |G| + |G|/J_n FMAs, row sums J_n + J_n(J_n+1)/2 FMAs
     G = math.prod(w.ranks)
-    fma = sum(G + G // Jn + Jn + Jn * (Jn + 1) // 2 for Jn in w.ranks) / N
-    flops_sweep = 2.0 * fma * nnz * N
-    sweep_s = op_ms["sweep_factors"] / 1e3
-    achieved = flops_sweep / sweep_s / 1e12
-    # algorithmic bytes of one factor sweep (all modes): per mode nnz((N-1)*4 + s_val) + (I_n+1)*8 +
-    # 2 I_n J_n s_f + I_n J_n (mask) + sum_{k != n} I_k J_k s_f
     s = 4 if w.dtype == "f32" else 8
-    bytes_sweep = 0
+    flops_mode, bytes_mode = [], []
     for n in range(N):
-        bytes_sweep += nnz * ((N - 1) * 4 + s) + (w.dims[n] + 1) * 8 + 2 * w.dims[n] * w.ranks[n] * s
-        bytes_sweep += w.dims[n] * w.ranks[n] + sum(w.dims[k] * w.ranks[k] * s for k in range(N) if k != n)
+        Jn = w.ranks[n]
+        flops_mode.append(2.0 * nnz * (G + G // Jn + Jn + Jn * (Jn + 1) // 2))
+        # per mode: nnz ((N-1) 4 + s_val) + (I_n+1) 8 + 2 I_n J_n s_f + I_n J_n (mask) + sum_{k != n} I_k J_k s_f
+        bytes_mode.append(nnz * ((N - 1) * 4 + s) + (w.dims[n] + 1) * 8 + 2 * w.dims[n] * Jn * s
+                          + w.dims[n] * Jn + sum(w.dims[k] * w.ranks[k] * s for k in range(N) if k != n))
+    launch_s = statistics.mean(mode_ms) / 1e3
+    flops_launch, bytes_launch = statistics.mean(flops_mode), statistics.mean(bytes_mode)
+    achieved = flops_launch / launch_s / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    roofline = {"bound": "alu", "kernel": "vest_sweep_factors (all modes: task kernels + fix-up)",
+    traffic, traffic_note = profiled_traffic(args.workload)
+    roofline = {"bound": "alu", "kernel": "vest_sweep_factors, one mode (sweep_task_kernel + fix-up), mean over modes",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "peak_source": f"FP32 FMA: {GB300_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz",
-                "traffic": None,
-                "algorithmic_flops_per_launch": flops_sweep, "algorithmic_bytes_per_launch": bytes_sweep,
-                "hbm_achieved_gbs": bytes_sweep / sweep_s / 1e9, "hbm_peak_gbs": hbm,
-                "hbm_frac": bytes_sweep / sweep_s / 1e9 / hbm, "hbm_peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+                "traffic": traffic, "traffic_source": traffic_note,
+                "launch_ms": launch_s * 1e3,
+                "algorithmic_flops_per_launch": flops_launch, "algorithmic_bytes_per_launch": bytes_launch,
+                "hbm_achieved_gbs": bytes_launch / launch_s / 1e9, "hbm_peak_gbs": hbm,
+                "hbm_frac": bytes_launch / launch_s / 1e9 / hbm,
+                "hbm_peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -344,7 +375,7 @@ def main():
                                       "step": "factor sweep (all modes) + core sweep + loss + responsibility + "
                                               "prune (pr=0)"}),
         "op_ms": op_ms,
-        "sweep_only": {"value": world * units_per_step / sweep_s, "unit": UNIT},
+        "sweep_only": {"value": world * units_per_step / (op_ms["sweep_factors"] / 1e3), "unit": UNIT},
         "final_loss": {"sq_err": final_loss[0], "objective": final_loss[3], "re": final_loss[4]},
         "roofline": roofline,
         "cpu_baseline": cpu,
