@@ -213,6 +213,19 @@ __device__ __forceinline__ void load_fibre(T (&v)[JN], const T* __restrict__ g) 
   }
 }
 
+// Minimum resident blocks per SM for the __launch_bounds__ of kernels that run the
+// contraction below with `threads` threads per block.  Without it ptxas keeps these kernels
+// at 64 registers and spills the per-entry fibre weights inside the contraction loop.  The
+// estimate counts the live registers of the loop (accumulators, fibre weights, one core
+// fibre, ~48 for addressing and loop state, `extra` for the caller's own live values) and asks for as many blocks as that allows.
+template <typename T, int JN, int JF, int E>
+constexpr int delta_min_blocks(int threads, int extra = 0) {
+  const int w = (int)sizeof(T) / 4;
+  const int need = E * JN * w + E * JF * w + JN * w + 48 + extra;
+  const int b = 65536 / (threads * need);
+  return b < 1 ? 1 : (b > 8 ? 8 : b);
+}
+
 template <typename T, int JN, int JF, int E>
 __device__ __forceinline__ void delta_slice(T (&d)[E][JN], const T (&w)[E], const T* __restrict__ go, int Jf,
                                             const T* const (&rowf)[E], const T (&rf)[E][JF > 0 ? JF : 1]) {

@@ -46,7 +46,7 @@ struct LossArgs {
 
 // E entries per thread (threadIdx.x + e * blockDim.x of each 256-entry task).
 template <typename T, int JN, int JF, int NSLOW, int E>
-__global__ void __launch_bounds__(kLossTask) loss_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ gcore,
+__global__ void __launch_bounds__(kLossTask / E, (delta_min_blocks<T, JN, JF, E>(kLossTask / E, JF > 0 ? 0 : 24))) loss_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ gcore,
                                                          LossArgs a, T* __restrict__ resid_csr0,
                                                          T* __restrict__ resid_coo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -106,7 +106,7 @@ struct SweepTerm {
 };
 
 template <typename T, int JN, int JF, int NSLOW, int MODE, int E>
-__global__ void __launch_bounds__(256) sweep_task_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ gcore,
+__global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 / E))) sweep_task_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ gcore,
                                                          SweepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ModeRoles& r = a.r;
