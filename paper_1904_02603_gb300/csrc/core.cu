@@ -31,11 +31,8 @@ namespace vest {
 constexpr int kCoreTask = 256;
 constexpr int kCoreMaxB = 128;
 constexpr int kCoreMaxM = 10;
-constexpr int kGramMaxP = 576;      // per-piece gram outputs per group
 constexpr int kGramKSplit = 64;     // fixed: reduction order does not depend on the device
 constexpr int kCorePassCtas = 1216;  // fixed likewise (8 per SM on 152 SMs)
-constexpr int kStatsEPT = 16;       // stats accumulators per thread
-constexpr int kCoreKmax = 64;       // row pieces per phase-2 round
 
 struct CoreBlock {
   int64_t s;  // suffix linear index over modes >= 2
@@ -113,166 +110,235 @@ __device__ __forceinline__ void suffix_weights(const DevModel<T>& M, const int32
 }
 
 // ================================================================== gram pass
+constexpr int kGramSgB = 16;  // suffixes per gram group (registers per lane: 2 x kGramSgB)
+
 struct GramArgs {
   int J0, J1;
   int q0, mq, nY;
   int64_t s0;
-  int Sg, P, kmax;
+  int Sg, P;
   int64_t nnz, ntasks;
   void* Y;         // [slots][P]
   int32_t* srow;   // [slots]: compacted mode-0 row of the slot, -1 if unused
 };
 
-// terms of the gram pass: p = sidx * nY + yi -> c(s)^2 * K(yi)
+// Gram pass for one j_1 chunk [q0, q0 + mq) and one group of Sg suffixes: for every row
+// piece (the part of a mode-0 row inside one 256-entry task, slot = row + task)
+//   Y(s, q, q') = sum over the piece of c(s)^2 a1[q0 + q] a1[q0 + q'],  q <= q',
+// stored at Y[slot][s * nY + packed(q, q')].  Each warp takes whole tasks (warp-strided) and
+// walks them 32 entries at a time: the lanes stage one entry each (row, c(s)^2 of the group,
+// the a1 values of the chunk); then every lane runs through the entries in order for its
+// pairs (q, q') = packed index lane, lane + 32 and all Sg suffixes, and writes the piece's
+// sums at a row change and at the end of the task.
 template <typename T>
-struct GramTerm {
-  const T* sC;  // [entry][Sg]
-  const T* sK;  // [entry][nY]
-  int Sg, nY;
-  __device__ TermPtrs<T> prep(int p) const { return TermPtrs<T>{sC + p / nY, sK + p % nY, Sg, nY}; }
-};
-
-template <typename T>
-__global__ void __launch_bounds__(kCoreTask) core_gram_pass_kernel(DevModel<T> M, DevMode<T> csr, GramArgs a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) core_gram_pass_kernel(DevModel<T> M, DevMode<T> csr, GramArgs a) {
+  constexpr int V = 16 / (int)sizeof(T);  // values per 16-byte shared-memory load
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int P = a.P, nY = a.nY, Sg = a.Sg, mq = a.mq;
-  size_t off = 0;
-  int64_t* sptr = reinterpret_cast<int64_t*>(smem_raw + off); off += (size_t)(kCoreTask + 2) * 8;
-  T* sK = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * nY * sizeof(T);
-  T* sC = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * Sg * sizeof(T);
-  off = (off + 15) & ~(size_t)15;
-  T* sAcc = reinterpret_cast<T*>(smem_raw + off); off += (size_t)a.kmax * P * sizeof(T);
-  T* sPart = reinterpret_cast<T*>(smem_raw + off);
-  __shared__ PieceScratch pscr;
-  const int R = *csr.nnzrows;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int mq = a.mq, nY = a.nY, Sg = a.Sg, P = a.P;
+  const int sgp = (Sg + V - 1) / V * V;            // c(s)^2 padded to whole 16-byte loads
+  const int ld = (sgp + mq + V - 1) / V * V;       // staged entry: c(s)^2, a1 chunk
+  T* st = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * ld;
+  int* sk = reinterpret_cast<int*>(reinterpret_cast<T*>(smem_raw) + (size_t)nwarps * 32 * ld) + warp * 32;
   T* Y = static_cast<T*>(a.Y);
-  for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
+  int qa[2], qb[2];
+  bool on[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int pr = lane + 32 * i;
+    on[i] = pr < nY;
+    int x = 0, y = 0;
+    if (on[i]) sym_decode(pr, mq, x, y);
+    qa[i] = x;
+    qb[i] = y;
+  }
+  T acc[2][kGramSgB];
+  const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw = (int64_t)gridDim.x * nwarps;
+  for (int64_t task = gw; task < a.ntasks; task += nw) {
     const int64_t t0 = task * kCoreTask, t1 = min(t0 + (int64_t)kCoreTask, a.nnz);
-    const int cnt = (int)(t1 - t0);
-    int64_t k0;
-    const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, sptr, &k0);
-    if ((int)threadIdx.x < cnt) {
-      const int64_t p = t0 + threadIdx.x;
-      const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * a.J1 + a.q0;
-      T v[kCoreMaxM];
-#pragma unroll
-      for (int q = 0; q < kCoreMaxM; ++q) v[q] = q < mq ? a1[q] : T(0);
-      T* k = sK + threadIdx.x * nY;
-      int yi = 0;
-#pragma unroll
-      for (int q = 0; q < kCoreMaxM; ++q)
-#pragma unroll
-        for (int q2 = q; q2 < kCoreMaxM; ++q2)
-          if (q2 < mq) k[yi++] = v[q] * v[q2];
-      T* c = sC + threadIdx.x * Sg;
-      suffix_weights<T>(M, csr.oidx, a.nnz, p, a.s0, Sg, c, 1);
-      for (int i = 0; i < Sg; ++i) c[i] *= c[i];
-    }
-    __syncthreads();
-    const GramTerm<T> f{sC, sK, Sg, nY};
-    for (int r0 = 0; r0 < nrows; r0 += a.kmax) {
-      const int nr = min(a.kmax, nrows - r0);
-      piece_sums<T>(sptr + r0, nr, t0, t1, P, sAcc, sPart, &pscr, f);
-      for (int kr = 0; kr < nr; ++kr) {
-        const int64_t slot = k0 + r0 + kr + task;
-        for (int pp = threadIdx.x; pp < P; pp += blockDim.x) Y[slot * P + pp] = sAcc[kr * P + pp];
-        if (threadIdx.x == 0) a.srow[slot] = (int32_t)(k0 + r0 + kr);
+    int cur = -1;
+    for (int64_t c0 = t0; c0 < t1; c0 += 32) {
+      const int64_t p = c0 + lane;
+      __syncwarp();
+      if (p < t1) {
+        sk[lane] = csr.rowk[p];
+        T* se = st + lane * ld;
+        suffix_weights<T>(M, csr.oidx, a.nnz, p, a.s0, Sg, se, 1);
+        for (int s = 0; s < Sg; ++s) se[s] *= se[s];
+        for (int s = Sg; s < sgp; ++s) se[s] = T(0);
+        const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * a.J1 + a.q0;
+        for (int q = 0; q < mq; ++q) se[sgp + q] = a1[q];
       }
-      __syncthreads();
+      __syncwarp();
+      const int n = (int)min((int64_t)32, t1 - c0);
+      for (int e = 0; e < n; ++e) {
+        const int k = sk[e];
+        const T* se = st + e * ld;
+        if (k != cur) {
+          if (cur >= 0) {
+            const int64_t slot = cur + task;
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+              if (on[i])
+#pragma unroll
+                for (int s = 0; s < kGramSgB; ++s)
+                  if (s < Sg) Y[slot * P + s * nY + lane + 32 * i] = acc[i][s];
+            if (lane == 0) a.srow[slot] = cur;
+          }
+          cur = k;
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int s = 0; s < kGramSgB; ++s) acc[i][s] = T(0);
+        }
+        T cv[kGramSgB];
+#pragma unroll
+        for (int s4 = 0; s4 < kGramSgB; s4 += V) {
+          if (s4 < Sg) {
+            if constexpr (sizeof(T) == 4) {
+              const float4 v = *reinterpret_cast<const float4*>(se + s4);
+              cv[s4] = v.x;
+              cv[s4 + 1] = v.y;
+              cv[s4 + 2] = v.z;
+              cv[s4 + 3] = v.w;
+            } else {
+              const double2 v = *reinterpret_cast<const double2*>(se + s4);
+              cv[s4] = v.x;
+              cv[s4 + 1] = v.y;
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < V; ++u) cv[s4 + u] = T(0);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          if (on[i]) {
+            const T kq = se[sgp + qa[i]] * se[sgp + qb[i]];
+#pragma unroll
+            for (int s = 0; s < kGramSgB; ++s)
+              if (s < Sg) acc[i][s] += cv[s] * kq;
+          }
+        }
+      }
+    }
+    if (cur >= 0) {
+      const int64_t slot = cur + task;
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+        if (on[i])
+#pragma unroll
+          for (int s = 0; s < kGramSgB; ++s)
+            if (s < Sg) Y[slot * P + s * nY + lane + 32 * i] = acc[i][s];
+      if (lane == 0) a.srow[slot] = cur;
     }
   }
 }
 
-// Z[ks][xi][p] = sum over the slots of split ks of X_slot[xi] * Y[slot][p], X = packed
-// upper a0 a0^T of the slot's row.  Tile 32 (xi) x 64 (p); 32-slot chunks in FP32,
-// Kahan across chunks.
+// X of every slot: Xs[slot][xi] = a0[ja] a0[jb] for the packed upper pair xi = (ja, jb)
+// of the slot's mode-0 row (0 for unused slots).  The slots are the same for every gram
+// group, so this runs once per core sweep.
+template <typename T>
+__global__ void core_gram_x_kernel(DevModel<T> M, DevMode<T> csr, const int32_t* __restrict__ srow, int64_t nslots,
+                                   int J0, int nX, T* __restrict__ Xs) {
+  const int64_t n = nslots * nX;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t slot = e / nX;
+    const int xi = (int)(e % nX);
+    const int32_t k = srow[slot];
+    T v = T(0);
+    if (k >= 0) {
+      int ja, jb;
+      sym_decode(xi, J0, ja, jb);
+      const T* a0 = M.A[0] + (int64_t)csr.nzrow[k] * J0;
+      v = a0[ja] * a0[jb];
+    }
+    Xs[e] = v;
+  }
+}
+
+// Z[ks][xi][p] = sum over the slots of split ks of Xs[slot][xi] * Y[slot][p].  CTA tile
+// 64 (xi) x 64 (p), 4 x 4 outputs per thread; slots staged CS at a time through registers
+// (the next chunk's loads are in flight while the current one is multiplied); each chunk
+// is summed in the storage type and added to the running sums with Kahan compensation.
 struct GemmArgs {
   int J0, nX, P;
   int64_t nslots;
+  const void* Xs;
   const void* Y;
   const int32_t* srow;
   double* part;  // [ks][nX][P]
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) core_gram_gemm_kernel(DevModel<T> M, DevMode<T> csr, GemmArgs a) {
-  __shared__ T sX[32][33];
-  __shared__ T sY[32][65];
-  __shared__ int2 xtab[32];
-  const int tiles_p = (a.P + 63) / 64;
-  const int tx0 = (blockIdx.x / tiles_p) * 32, tp0 = (blockIdx.x % tiles_p) * 64;
-  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
-  const int ks = blockIdx.y;
-  const int64_t per = ceil_div(a.nslots, (int64_t)gridDim.y);
-  const int64_t sl0 = ks * per, sl1 = min(a.nslots, sl0 + per);
-  if (threadIdx.x < 32) {
-    const int xi = tx0 + threadIdx.x;
-    int ja = 0, jb = 0;
-    if (xi < a.nX) sym_decode(xi, a.J0, ja, jb);
-    xtab[threadIdx.x] = make_int2(xi < a.nX ? ja : -1, jb);
-  }
+__global__ void __launch_bounds__(256, 2) core_gram_gemm_kernel(GemmArgs a) {
+  constexpr int CS = sizeof(T) == 4 ? 32 : 16;  // slots per chunk
+  constexpr int NX = CS * 64 / 256;             // staged X (and Y) values per thread
+  __shared__ __align__(16) T sX[CS][64];
+  __shared__ __align__(16) T sY[CS][64];
+  const T* Xs = static_cast<const T*>(a.Xs);
   const T* Y = static_cast<const T*>(a.Y);
-  T run_s[4][2], run_c[4][2];
+  const int tiles_p = (a.P + 63) / 64;
+  const int tx0 = (blockIdx.x / tiles_p) * 64, tp0 = (blockIdx.x % tiles_p) * 64;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const int64_t per = ceil_div(a.nslots, (int64_t)gridDim.y);
+  const int64_t sl0 = blockIdx.y * per, sl1 = min(a.nslots, sl0 + per);
+  T xr[NX], yr[NX];
+  auto load = [&](int64_t c0) {
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      const int e = threadIdx.x + 256 * i, cs = e >> 6, l = e & 63;
+      const int64_t slot = c0 + cs;
+      const bool in = slot < sl1 && a.srow[slot] >= 0;
+      xr[i] = (in && tx0 + l < a.nX) ? Xs[slot * a.nX + tx0 + l] : T(0);
+      yr[i] = (in && tp0 + l < a.P) ? Y[slot * a.P + tp0 + l] : T(0);
+    }
+  };
+  T run_s[4][4], run_c[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) run_s[i][j] = run_c[i][j] = T(0);
-  __syncthreads();
-  for (int64_t c0 = sl0; c0 < sl1; c0 += 32) {
-    // stage 32 slots: X from the slot's a0 row, Y tile
-    for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
-      const int cs = i >> 5, xl = i & 31;
-      const int64_t slot = c0 + cs;
-      T xv = T(0);
-      const int2 jt = xtab[xl];
-      if (slot < sl1 && jt.x >= 0) {
-        const int32_t k = a.srow[slot];
-        if (k >= 0) {
-          const T* a0 = M.A[0] + (int64_t)csr.nzrow[k] * a.J0;
-          xv = a0[jt.x] * a0[jt.y];
-        }
-      }
-      sX[cs][xl] = xv;
-    }
-    for (int i = threadIdx.x; i < 32 * 64; i += blockDim.x) {
-      const int cs = i >> 6, pl = i & 63;
-      const int64_t slot = c0 + cs;
-      const int p = tp0 + pl;
-      T yv = T(0);
-      if (slot < sl1 && p < a.P && a.srow[slot] >= 0) yv = Y[slot * a.P + p];
-      sY[cs][pl] = yv;
+    for (int j = 0; j < 4; ++j) run_s[i][j] = run_c[i][j] = T(0);
+  if (sl0 < sl1) load(sl0);
+  for (int64_t c0 = sl0; c0 < sl1; c0 += CS) {
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      const int e = threadIdx.x + 256 * i, cs = e >> 6, l = e & 63;
+      sX[cs][l] = xr[i];
+      sY[cs][l] = yr[i];
     }
     __syncthreads();
-    T acc[4][2];
+    if (c0 + CS < sl1) load(c0 + CS);
+    T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 2; ++j) acc[i][j] = T(0);
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 #pragma unroll 8
-    for (int cs = 0; cs < 32; ++cs) {
-      T xv[4], yv[2];
+    for (int cs = 0; cs < CS; ++cs) {
+      T xv[4], yv[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) xv[i] = sX[cs][ty + 8 * i];
+      for (int i = 0; i < 4; ++i) xv[i] = sX[cs][ty * 4 + i];
 #pragma unroll
-      for (int j = 0; j < 2; ++j) yv[j] = sY[cs][tx + 32 * j];
+      for (int j = 0; j < 4; ++j) yv[j] = sY[cs][tx * 4 + j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) acc[i][j] += xv[i] * yv[j];
+        for (int j = 0; j < 4; ++j) acc[i][j] += xv[i] * yv[j];
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 2; ++j) CoreAcc<T>::add(run_s[i][j], run_c[i][j], acc[i][j]);
+      for (int j = 0; j < 4; ++j) CoreAcc<T>::add(run_s[i][j], run_c[i][j], acc[i][j]);
     __syncthreads();
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int xi = tx0 + ty + 8 * i, p = tp0 + tx + 32 * j;
+    for (int j = 0; j < 4; ++j) {
+      const int xi = tx0 + ty * 4 + i, p = tp0 + tx * 4 + j;
       if (xi < a.nX && p < a.P)
-        a.part[((size_t)ks * a.nX + xi) * a.P + p] = CoreAcc<T>::value(run_s[i][j], run_c[i][j]);
+        a.part[((size_t)blockIdx.y * a.nX + xi) * a.P + p] = CoreAcc<T>::value(run_s[i][j], run_c[i][j]);
     }
 }
 
@@ -323,20 +389,34 @@ __global__ void core_u_kernel(DevModel<T> M, const int32_t* __restrict__ nzrow, 
   }
 }
 
+// A0c[k] = a0 row of the k-th non-empty mode-0 row (the core sweep leaves A^(0) unchanged).
+template <typename T>
+__global__ void core_a0c_kernel(DevModel<T> M, const int32_t* __restrict__ nzrow, const int32_t* __restrict__ nnzrows,
+                                int J0, T* __restrict__ A0c) {
+  const int64_t n = (int64_t)*nnzrows * J0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    A0c[e] = M.A[0][(int64_t)nzrow[e / J0] * J0 + e % J0];
+}
+
 // One streaming pass per block.  Each warp takes 32 consecutive entries at a
 // time: it applies the previous block's Delta to r (r -= c' a1 . u(row)), forms
 // h(q) = r a1[q0 + q] c, adds h over each row segment inside the warp, and every
 // segment head adds a0[row] (x) h into the warp's g accumulators (lane l holds
-// entries l, l + 32, ...; Kahan across heads).  g is linear in the rows, so row
-// segments cut by chunk edges need no fix-up.
+// elements l, l + 32, ...; Kahan across heads).  g is linear in the rows, so row
+// segments cut by chunk edges need no fix-up.  All gathers of a chunk (a1, the
+// suffix weights, u, and the head lanes' a0 rows from A0c) are issued together
+// after the coalesced index loads.
 template <typename T>
-__global__ void __launch_bounds__(256) core_g_pass_kernel(DevModel<T> M, DevMode<T> csr, T* r, const T* __restrict__ U,
-                                                          GPassArgs a) {
+__global__ void __launch_bounds__(256, 3) core_g_pass_kernel(DevModel<T> M, DevMode<T> csr, T* r, const T* __restrict__ U,
+                                                          const T* __restrict__ A0c, GPassArgs a) {
   constexpr int kPer = kCoreMaxB / 32;
   __shared__ T sh[8][kCoreMaxM];
   __shared__ double sw[8][kCoreMaxB];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int J0 = a.J0, m = a.cur.m, b = a.cur.b, mp = a.has_prev ? a.prev.m : 0;
+  T* sa = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * J0;  // a0 row of each head lane
+  const bool same_q = a.has_prev && a.prev.q0 == a.cur.q0;
   T as[kPer], ac[kPer];
 #pragma unroll
   for (int i = 0; i < kPer; ++i) as[i] = ac[i] = T(0);
@@ -346,12 +426,23 @@ __global__ void __launch_bounds__(256) core_g_pass_kernel(DevModel<T> M, DevMode
     const int64_t p = ch * 32 + lane;
     const bool valid = p < a.nnz;
     const int k = valid ? csr.rowk[p] : -1 - lane;
+    const int kup = __shfl_up_sync(0xffffffffu, k, 1);
+    const bool head = valid && (lane == 0 || kup != k);
     T h[kCoreMaxM];
 #pragma unroll
     for (int q = 0; q < kCoreMaxM; ++q) h[q] = T(0);
+    __syncwarp();
+    if (head) {
+      const T* a0 = A0c + (int64_t)k * J0;
+      for (int j = 0; j < J0; ++j) sa[lane * J0 + j] = a0[j];
+    }
     if (valid) {
       const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * a.J1;
       T rv = r[p];
+      T v[kCoreMaxM];
+#pragma unroll
+      for (int q = 0; q < kCoreMaxM; ++q)
+        if (q < m) v[q] = a1[a.cur.q0 + q];
       if (a.has_prev) {
         T cp;
         suffix_weights<T>(M, csr.oidx, a.nnz, p, a.prev.s, 1, &cp, 1);
@@ -359,7 +450,7 @@ __global__ void __launch_bounds__(256) core_g_pass_kernel(DevModel<T> M, DevMode
         T acc = T(0);
 #pragma unroll
         for (int q = 0; q < kCoreMaxM; ++q)
-          if (q < mp) acc += a1[a.prev.q0 + q] * u[q];
+          if (q < mp) acc += (same_q ? v[q] : a1[a.prev.q0 + q]) * u[q];
         rv -= cp * acc;
         r[p] = rv;
       }
@@ -368,7 +459,7 @@ __global__ void __launch_bounds__(256) core_g_pass_kernel(DevModel<T> M, DevMode
       const T rc = rv * c;
 #pragma unroll
       for (int q = 0; q < kCoreMaxM; ++q)
-        if (q < m) h[q] = rc * a1[a.cur.q0 + q];
+        if (q < m) h[q] = rc * v[q];
     }
     // segmented suffix sums: lane l ends with the sum over its row from l to the chunk end
 #pragma unroll
@@ -380,23 +471,20 @@ __global__ void __launch_bounds__(256) core_g_pass_kernel(DevModel<T> M, DevMode
         if (lane + o < 32 && ko == k) h[q] += v;
       }
     }
-    const int kup = __shfl_up_sync(0xffffffffu, k, 1);
-    unsigned heads = __ballot_sync(0xffffffffu, valid && (lane == 0 || kup != k));
+    unsigned heads = __ballot_sync(0xffffffffu, head);
     while (heads) {
       const int hl = __ffs(heads) - 1;
       heads &= heads - 1;
-      const int kk = __shfl_sync(0xffffffffu, k, hl);
       if (lane == hl) {
 #pragma unroll
         for (int q = 0; q < kCoreMaxM; ++q)
           if (q < m) sh[warp][q] = h[q];
       }
       __syncwarp();
-      const T* a0 = M.A[0] + (int64_t)csr.nzrow[kk] * J0;
 #pragma unroll
       for (int i = 0; i < kPer; ++i) {
         const int e = lane + 32 * i;
-        if (e < b) CoreAcc<T>::add(as[i], ac[i], a0[e % J0] * sh[warp][e / J0]);
+        if (e < b) CoreAcc<T>::add(as[i], ac[i], sa[hl * J0 + e % J0] * sh[warp][e / J0]);
       }
       __syncwarp();
     }
@@ -437,8 +525,10 @@ __global__ void core_vec_merge_kernel(const double* __restrict__ part, int nctas
 }
 
 // Exact sequential updates of one block (Eq. 12 / Eq. 14) by one warp: lane
-// k % 32 holds the running sum_alpha r P(k) of element k; after each update
-// every lane subtracts Delta_k M_kl from the elements l > k it holds.
+// k % 32 holds the running sum_alpha r P(k) of element k, its value, mask and the
+// reciprocal of its denominator.  At step k the owning lane computes Delta_k alone
+// and broadcasts it; every lane then subtracts Delta_k M_kl from the elements l > k
+// it holds.
 template <typename T>
 __global__ void core_solve_kernel(DevModel<T> M, CoreBlock blk, int J0, int J1, int reg, double lambda,
                                   const double* gram, const double* __restrict__ g, double* __restrict__ dout) {
@@ -449,55 +539,49 @@ __global__ void core_solve_kernel(DevModel<T> M, CoreBlock blk, int J0, int J1, 
   for (int e = threadIdx.x; e < b * (b + 1) / 2; e += blockDim.x) sgram[e] = gram[e];
   __syncthreads();
   if (threadIdx.x >= 32) return;
-  gram = sgram;
-  // lane holds, for its elements l = lane + 32 i: the running sum, the current value, the mask
-  double grad[kPer], gval[kPer];
-  int gmask[kPer];
   auto lin_of = [&](int k) {
     return (int64_t)(k % J0) + (int64_t)J0 * (blk.q0 + k / J0) + (int64_t)J0 * J1 * blk.s;
   };
+  double grad[kPer], gval[kPer], mkk[kPer], inv[kPer];
+  bool free_[kPer];
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
     const int l = lane + 32 * i;
-    grad[i] = l < b ? g[l] : 0.0;
-    gval[i] = l < b ? (double)M.G[lin_of(l)] : 0.0;
-    gmask[i] = l < b ? (int)M.Gmask[lin_of(l)] : 1;
+    const bool in = l < b;
+    grad[i] = in ? g[l] : 0.0;
+    gval[i] = in ? (double)M.G[lin_of(l)] : 0.0;
+    free_[i] = in && !M.Gmask[lin_of(l)];
+    mkk[i] = in ? sgram[sym_index(l, l, b)] : 1.0;
+    // Eq. 12: new = num / (lambda + M_kk); Eq. 14: new = -(g -/+ lambda) / (2 M_kk)
+    inv[i] = reg == VEST_REG_L1 ? 1.0 / (2.0 * mkk[i]) : 1.0 / (lambda + mkk[i]);
   }
   for (int k = 0; k < b; ++k) {
-    const int64_t lin = lin_of(k);
-    double gk = 0.0, gold = 0.0;
-    int mk = 1;
-#pragma unroll
-    for (int i = 0; i < kPer; ++i)
-      if (k / 32 == i) {
-        gk = grad[i];
-        gold = gval[i];
-        mk = gmask[i];
-      }
-    gk = __shfl_sync(0xffffffffu, gk, k & 31);
-    gold = __shfl_sync(0xffffffffu, gold, k & 31);
-    mk = __shfl_sync(0xffffffffu, mk, k & 31);
     double dk = 0.0;
-    if (!mk) {
-      const double mkk = gram[sym_index(k, k, b)];
-      const double num = gk + gold * mkk;
-      double nv;
-      if (reg == VEST_REG_L1) {
-        const double gcv = -2.0 * num, dc = 2.0 * mkk;
-        nv = gcv > lambda ? (lambda - gcv) / dc : (gcv < -lambda ? -(lambda + gcv) / dc : 0.0);
-      } else {
-        nv = num / (lambda + mkk);
+    if (lane == (k & 31)) {
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        if (k / 32 == i && free_[i]) {
+          const double num = grad[i] + gval[i] * mkk[i];
+          double nv;
+          if (reg == VEST_REG_L1) {
+            const double gcv = -2.0 * num;
+            nv = gcv > lambda ? (lambda - gcv) * inv[i] : (gcv < -lambda ? -(lambda + gcv) * inv[i] : 0.0);
+          } else {
+            nv = num * inv[i];
+          }
+          const T st = (T)nv;
+          dk = (double)st - gval[i];
+          M.G[lin_of(k)] = st;
+        }
       }
-      const T st = (T)nv;
-      dk = (double)st - gold;
-      if (lane == 0) M.G[lin] = st;
+      dout[k] = dk;
     }
-    if (lane == 0) dout[k] = dk;
+    dk = __shfl_sync(0xffffffffu, dk, k & 31);
     if (dk != 0.0) {
 #pragma unroll
       for (int i = 0; i < kPer; ++i) {
         const int l = lane + 32 * i;
-        if (l > k && l < b) grad[i] -= dk * gram[sym_index(k, l, b)];
+        if (l > k && l < b) grad[i] -= dk * sgram[sym_index(k, l, b)];
       }
     }
   }
@@ -509,90 +593,155 @@ __global__ void core_solve_kernel(DevModel<T> M, CoreBlock blk, int J0, int J1, 
 struct StatsArgs {
   int J0, J1;
   int64_t s0;
-  int Sg, SJ, P, kmax;
+  int Sg, SJ;
   int64_t nnz, ntasks;
-  double* part;  // [ctas][2 * J0 * SJ]
+  size_t red_off;  // byte offset in shared memory of the FP64 warp reduction
+  double* part;    // [ctas][2 * J0 * SJ]
 };
 
-template <typename T>
-struct StatsTerm {
-  const T* sR;
-  const T* sW;
-  int SJ;
-  __device__ TermPtrs<T> prep(int p) const {
-    if (p < SJ) return TermPtrs<T>{sR, sW + p, 1, SJ};
-    return TermPtrs<T>{sW + (p - SJ), sW + (p - SJ), SJ, SJ};
-  }
-};
+// Streams (pairs (j_1, s) of the group) per lane in the stats pass.
+__host__ __device__ constexpr int stats_spl(int J0B) { return J0B <= 12 ? 2 : 1; }
 
-template <typename T>
-__global__ void __launch_bounds__(kCoreTask) core_stats_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ r,
-                                                               StatsArgs a) {
+// Shared memory of the stats pass: per warp the staged entries and the running sums.
+__host__ __device__ inline size_t stats_stage_elems(int J0, int J1, int Sg) { return (size_t)32 * (J0 + J1 + Sg + 1); }
+__host__ __device__ inline size_t stats_run_elems(int J0, int spl) { return (size_t)2 * 2 * J0 * 32 * spl; }
+
+// Stats pass for one group of Sg suffixes: for every core element (j0, j1, s) of the group
+//   g(j0, j1, s)    = sum_alpha r a0[j0] a1[j1] c(s)
+//   diag(j0, j1, s) = sum_alpha (a0[j0] a1[j1] c(s))^2.
+// Each warp takes whole 256-entry tasks of the mode-0 CSR (warp-strided over the grid) and
+// walks them 32 entries at a time: the lanes stage one entry each (row, r, a0 row, a1 row,
+// c(s) of the group) in shared memory; then every lane runs through the 32 entries in order
+// for its own pairs (j1, s), summing h1 = sum r y and h2 = sum y^2 (y = a1[j1] c(s)) while
+// the row stays the same.  At a row change and at the end of the task the lane adds
+// a0 (x) h1 and a0^2 (x) h2 into its task sums; at the end of the task those go into the
+// warp's running sums in shared memory (Kahan).  Warps are combined in warp order in FP64,
+// one partial per CTA.
+template <typename T, int J0B>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
+    core_stats_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ r, StatsArgs a) {
+  constexpr int SPL = stats_spl(J0B);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int J0 = a.J0, SJ = a.SJ, P = a.P;
-  size_t off = 0;
-  int64_t* sptr = reinterpret_cast<int64_t*>(smem_raw + off); off += (size_t)(kCoreTask + 2) * 8;
-  T* sA0 = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * J0 * sizeof(T);
-  T* sW = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * SJ * sizeof(T);
-  T* sR = reinterpret_cast<T*>(smem_raw + off); off += (size_t)kCoreTask * sizeof(T);
-  off = (off + 15) & ~(size_t)15;
-  T* sAcc = reinterpret_cast<T*>(smem_raw + off); off += (size_t)a.kmax * P * sizeof(T);
-  T* sPart = reinterpret_cast<T*>(smem_raw + off);
-  __shared__ PieceScratch pscr;
-  const int nacc = 2 * J0 * SJ;
-  T rs[kStatsEPT], rc[kStatsEPT], tacc[kStatsEPT];
-#pragma unroll
-  for (int i = 0; i < kStatsEPT; ++i) rs[i] = rc[i] = T(0);
-  const int R = *csr.nnzrows;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
+  const int J0 = a.J0, J1 = a.J1, Sg = a.Sg, SJ = a.SJ;
+  const int ld = J0 + J1 + Sg + 1;  // staged entry: a0 row, a1 row, c(s), r
+  T* base = reinterpret_cast<T*>(smem_raw);
+  const size_t stage = stats_stage_elems(J0, J1, Sg), run = stats_run_elems(J0, SPL);
+  T* st = base + (size_t)warp * stage;
+  // running sums of this lane: [kind][j0][i] x (sum, comp), lane-interleaved
+  T* rs = base + (size_t)nwarps * stage + (size_t)warp * run;
+  int* sk = reinterpret_cast<int*>(base + (size_t)nwarps * (stage + run)) + warp * 32;
+  // [2][J0][SJ] after the pass: over the staged entries, never over the running sums
+  double* red = reinterpret_cast<double*>(smem_raw + a.red_off);
+  for (size_t e = lane; e < run; e += 32) rs[e] = T(0);
+  int qo[SPL], so[SPL];
+  bool on[SPL];
+#pragma unroll
+  for (int i = 0; i < SPL; ++i) {
+    const int pr = lane + 32 * i;
+    on[i] = pr < SJ;
+    qo[i] = on[i] ? pr % J1 : 0;
+    so[i] = on[i] ? pr / J1 : 0;
+  }
+  T t1s[J0B][SPL], t2s[J0B][SPL];
+  T a0r[J0B];
+  T h1[SPL], h2[SPL];
+  const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw = (int64_t)gridDim.x * nwarps;
+  for (int64_t task = gw; task < a.ntasks; task += nw) {
     const int64_t t0 = task * kCoreTask, t1 = min(t0 + (int64_t)kCoreTask, a.nnz);
-    const int cnt = (int)(t1 - t0);
-    int64_t k0;
-    const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, sptr, &k0);
-    for (int k = warp; k < nrows; k += nwarps) {
-      const int64_t row = csr.nzrow[k0 + k];
-      for (int j = lane; j < J0; j += 32) sA0[k * J0 + j] = M.A[0][row * J0 + j];
-    }
-    if ((int)threadIdx.x < cnt) {
-      const int64_t p = t0 + threadIdx.x;
-      const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * a.J1;
-      T* w = sW + threadIdx.x * SJ;
-      suffix_weights<T>(M, csr.oidx, a.nnz, p, a.s0, a.Sg, w, a.J1);  // c(s) at w[s * J1]
-      for (int si = 0; si < a.Sg; ++si) {
-        const T c = w[si * a.J1];
-        for (int q = 0; q < a.J1; ++q) w[si * a.J1 + q] = a1[q] * c;
+#pragma unroll
+    for (int j = 0; j < J0B; ++j)
+#pragma unroll
+      for (int i = 0; i < SPL; ++i) t1s[j][i] = t2s[j][i] = T(0);
+    int cur = -1;
+    for (int64_t c0 = t0; c0 < t1; c0 += 32) {
+      const int64_t p = c0 + lane;
+      __syncwarp();
+      if (p < t1) {
+        const int k = csr.rowk[p];
+        sk[lane] = k;
+        T* se = st + lane * ld;
+        const T* a0 = M.A[0] + (int64_t)csr.nzrow[k] * J0;
+        for (int j = 0; j < J0; ++j) se[j] = a0[j];
+        const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * J1;
+        for (int q = 0; q < J1; ++q) se[J0 + q] = a1[q];
+        suffix_weights<T>(M, csr.oidx, a.nnz, p, a.s0, Sg, se + J0 + J1, 1);
+        se[J0 + J1 + Sg] = r[p];
       }
-      sR[threadIdx.x] = r[p];
-    }
-    __syncthreads();
+      __syncwarp();
+      const int n = (int)min((int64_t)32, t1 - c0);
+      for (int e = 0; e < n; ++e) {
+        const int k = sk[e];
+        const T* se = st + e * ld;
+        if (k != cur) {
+          if (cur >= 0) {
 #pragma unroll
-    for (int i = 0; i < kStatsEPT; ++i) tacc[i] = T(0);
-    const StatsTerm<T> f{sR, sW, SJ};
-    for (int r0 = 0; r0 < nrows; r0 += a.kmax) {
-      const int nr = min(a.kmax, nrows - r0);
-      piece_sums<T>(sptr + r0, nr, t0, t1, P, sAcc, sPart, &pscr, f);
+            for (int j = 0; j < J0B; ++j)
 #pragma unroll
-      for (int i = 0; i < kStatsEPT; ++i) {
-        const int e = threadIdx.x + i * blockDim.x;
-        if (e >= nacc) continue;
-        const int kind = e / (J0 * SJ), rem = e % (J0 * SJ);
-        const int j0 = rem % J0, sq = rem / J0;
-        for (int kr = 0; kr < nr; ++kr) {
-          const T av = sA0[(r0 + kr) * J0 + j0];
-          tacc[i] += kind == 0 ? av * sAcc[kr * P + sq] : av * av * sAcc[kr * P + SJ + sq];
+              for (int i = 0; i < SPL; ++i) {
+                t1s[j][i] += a0r[j] * h1[i];
+                t2s[j][i] += a0r[j] * a0r[j] * h2[i];
+              }
+          }
+          cur = k;
+#pragma unroll
+          for (int j = 0; j < J0B; ++j) a0r[j] = j < J0 ? se[j] : T(0);
+#pragma unroll
+          for (int i = 0; i < SPL; ++i) h1[i] = h2[i] = T(0);
+        }
+        const T rv = se[J0 + J1 + Sg];
+#pragma unroll
+        for (int i = 0; i < SPL; ++i) {
+          const T y = se[J0 + qo[i]] * se[J0 + J1 + so[i]];
+          h1[i] += rv * y;
+          h2[i] += y * y;
         }
       }
-      __syncthreads();
+    }
+    if (cur >= 0) {
+#pragma unroll
+      for (int j = 0; j < J0B; ++j)
+#pragma unroll
+        for (int i = 0; i < SPL; ++i) {
+          t1s[j][i] += a0r[j] * h1[i];
+          t2s[j][i] += a0r[j] * a0r[j] * h2[i];
+        }
     }
 #pragma unroll
-    for (int i = 0; i < kStatsEPT; ++i) CoreAcc<T>::add(rs[i], rc[i], tacc[i]);
-  }
+    for (int j = 0; j < J0B; ++j) {
+      if (j < J0) {
 #pragma unroll
-  for (int i = 0; i < kStatsEPT; ++i) {
-    const int e = threadIdx.x + i * blockDim.x;
-    if (e < nacc) a.part[(size_t)blockIdx.x * nacc + e] = CoreAcc<T>::value(rs[i], rc[i]);
+        for (int i = 0; i < SPL; ++i) {
+          T* x1 = rs + ((size_t)(0 * J0 + j) * SPL + i) * 64 + lane;
+          T* x2 = rs + ((size_t)(1 * J0 + j) * SPL + i) * 64 + lane;
+          CoreAcc<T>::add(x1[0], x1[32], t1s[j][i]);
+          CoreAcc<T>::add(x2[0], x2[32], t2s[j][i]);
+        }
+      }
+    }
   }
+  // warps in order, FP64: red[kind * J0 * SJ + j0 + J0 * pair]
+  __syncthreads();
+  const int nacc = 2 * J0 * SJ;
+  for (int w = 0; w < nwarps; ++w) {
+    if (warp == w) {
+      for (int j = 0; j < J0; ++j) {
+#pragma unroll
+        for (int i = 0; i < SPL; ++i) {
+          if (on[i]) {
+            const T* x1 = rs + ((size_t)(0 * J0 + j) * SPL + i) * 64 + lane;
+            const T* x2 = rs + ((size_t)(1 * J0 + j) * SPL + i) * 64 + lane;
+            const int e1 = j + J0 * (lane + 32 * i), e2 = J0 * SJ + e1;
+            const double v1 = CoreAcc<T>::value(x1[0], x1[32]), v2 = CoreAcc<T>::value(x2[0], x2[32]);
+            red[e1] = w == 0 ? v1 : red[e1] + v1;
+            red[e2] = w == 0 ? v2 : red[e2] + v2;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nacc; e += blockDim.x) a.part[(size_t)blockIdx.x * nacc + e] = red[e];
 }
 
 // Delta and Resp of the group's core elements: lin = j0 + J0 (j1 + J1 s).
@@ -634,16 +783,15 @@ static CorePlan core_plan(const int32_t* J, int N, int64_t nnz, int64_t cap0) {
   c.nmmax = c.bmax * (c.bmax + 1) / 2;
   c.nX = c.J0 * (c.J0 + 1) / 2;
   c.nYmax = c.m * (c.m + 1) / 2;
-  c.SgMax = (int)std::max<int64_t>(1, std::min<int64_t>(c.S, kGramMaxP / c.nYmax));
+  c.SgMax = (int)std::min<int64_t>(c.S, kGramSgB);
   c.Pmax = 0;
   for (int q0 = 0; q0 < c.J1; q0 += c.m) {  // the last j_1 chunk may be narrower and take more suffixes
     const int mq = std::min(c.m, c.J1 - q0), nY = mq * (mq + 1) / 2;
-    const int sg = (int)std::max<int64_t>(1, std::min<int64_t>(c.S, kGramMaxP / nY));
-    c.Pmax = std::max(c.Pmax, sg * nY);
+    c.Pmax = std::max(c.Pmax, c.SgMax * nY);
   }
-  // stats: 2 * SJ outputs per piece <= 512, 2 * J0 * SJ accumulators <= kStatsEPT * 256
-  int sg = (int)std::max<int64_t>(1, std::min<int64_t>(c.S, 256 / c.J1));
-  while (sg > 1 && 2 * c.J0 * sg * c.J1 > kStatsEPT * kCoreTask) --sg;
+  // stats: 32 * stats_spl streams (j1, s) per group
+  const int streams = 32 * stats_spl(jn_bucket(c.J0));
+  const int sg = (int)std::max<int64_t>(1, std::min<int64_t>(c.S, streams / c.J1));
   c.SgStats = sg;
   c.SJ = sg * c.J1;
   c.slots = cap0 + ceil_div(std::max<int64_t>(nnz, 1), kCoreTask) + 1;
@@ -654,9 +802,10 @@ size_t core_scratch_bytes(const vest_model* m, int64_t nnz, int64_t cap0, size_t
                           size_t* part_bytes) {
   const CorePlan c = core_plan(m->ranks, m->order, nnz, cap0);
   const size_t sT = m->dtype == VEST_F64 ? 8 : 4;
-  // per-piece gram statistics, later reused for u per non-empty mode-0 row (cap0 x kCoreMaxM)
-  *y_bytes = align_up(std::max((size_t)c.slots * c.Pmax, (size_t)(cap0 + 1) * kCoreMaxM) * sT) +
-             align_up((size_t)c.slots * 4);
+  // per-piece gram statistics, later reused for u and the a0 row of every non-empty mode-0 row
+  // (cap0 x (kCoreMaxM + J0))
+  *y_bytes = align_up(std::max((size_t)c.slots * c.Pmax, (size_t)(cap0 + 1) * (kCoreMaxM + c.J0)) * sT) +
+             align_up((size_t)c.slots * 4) + align_up((size_t)c.slots * c.nX * sT);
   // the gram region also holds the responsibility sums (2 * J0 * SJ doubles)
   *gram_bytes = align_up(std::max((size_t)c.nblocks * c.nmmax, (size_t)2 * c.J0 * c.SJ) * 8);
   const size_t gemm = (size_t)kGramKSplit * c.nX * c.Pmax * 8;
@@ -667,28 +816,47 @@ size_t core_scratch_bytes(const vest_model* m, int64_t nnz, int64_t cap0, size_t
 }
 
 template <typename T>
-static size_t smem_gram(int nY, int Sg, int P, int kmax) {
-  size_t off = (size_t)(kCoreTask + 2) * 8 + (size_t)kCoreTask * nY * sizeof(T) + (size_t)kCoreTask * Sg * sizeof(T);
-  off = (off + 15) & ~(size_t)15;
-  return off + (size_t)kmax * P * sizeof(T) + (size_t)kMaxLongPieces * P * sizeof(T);
+static size_t smem_gram(int mq, int Sg) {
+  const int V = 16 / (int)sizeof(T);
+  const int sgp = (Sg + V - 1) / V * V, ld = (sgp + mq + V - 1) / V * V;
+  return (size_t)8 * 32 * ld * sizeof(T) + (size_t)8 * 32 * 4;
 }
 
+// Shared memory of the stats pass; *red_off receives the offset of the FP64 warp
+// reduction: inside the staging region when it fits there, else behind everything.
 template <typename T>
-static size_t smem_stats(int J0, int SJ, int P, int kmax) {
-  size_t off = (size_t)(kCoreTask + 2) * 8 + (size_t)kCoreTask * J0 * sizeof(T) + (size_t)kCoreTask * SJ * sizeof(T) +
-               (size_t)kCoreTask * sizeof(T);
-  off = (off + 15) & ~(size_t)15;
-  return off + (size_t)kmax * P * sizeof(T) + (size_t)kMaxLongPieces * P * sizeof(T);
+static size_t smem_stats(int J0, int J1, int Sg, int SJ, int nwarps, size_t* red_off = nullptr) {
+  const int spl = stats_spl(jn_bucket(J0));
+  const size_t pass = (size_t)nwarps * (stats_stage_elems(J0, J1, Sg) + stats_run_elems(J0, spl)) * sizeof(T) +
+                      (size_t)nwarps * 32 * 4;
+  const size_t red = (size_t)2 * J0 * SJ * 8;
+  const bool inside = red <= (size_t)nwarps * stats_stage_elems(J0, J1, Sg) * sizeof(T);
+  if (red_off) *red_off = inside ? 0 : align_up(pass, 16);
+  return inside ? pass : align_up(pass, 16) + red;
 }
 
+// Warps per CTA of the stats pass: 8 unless the shared memory would exceed 200 KB.
 template <typename T>
-static int kmax_for(int P) {
-  return (int)std::max<size_t>(1, std::min<size_t>(kCoreKmax, (48 * 1024) / ((size_t)P * sizeof(T))));
+static int stats_warps(int J0, int J1, int Sg, int SJ) {
+  int w = 8;
+  while (w > 1 && smem_stats<T>(J0, J1, Sg, SJ, w) > 200 * 1024) w /= 2;
+  return w;
+}
+
+template <typename T, int J0B>
+static vest_status launch_stats(const DevModel<T>& M, const DevMode<T>& csr, const T* r, const StatsArgs& a, int grid,
+                                int nwarps, size_t smem, cudaStream_t s) {
+  auto kern = core_stats_kernel<T, J0B>;
+  VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, 32 * nwarps, smem, s>>>(M, csr, r, a);
+  VEST_LAUNCH("core_stats_kernel");
+  return VEST_OK;
 }
 
 struct CoreBufs {
   void* Y;
   int32_t* srow;
+  void* Xs;
   double* gram;
   double* part;
   double* small;
@@ -701,7 +869,8 @@ static CoreBufs core_bufs(const vest_index* ix, const vest_model* m, char* scrat
   char* base = scratch + plan.off_core;
   b.Y = base;
   b.srow = reinterpret_cast<int32_t*>(
-      base + align_up(std::max((size_t)c.slots * c.Pmax, (size_t)(ix->mode[0].cap + 1) * kCoreMaxM) * sT));
+      base + align_up(std::max((size_t)c.slots * c.Pmax, (size_t)(ix->mode[0].cap + 1) * (kCoreMaxM + c.J0)) * sT));
+  b.Xs = reinterpret_cast<char*>(b.srow) + align_up((size_t)c.slots * 4);
   size_t yb, gb, pb;
   core_scratch_bytes(m, ix->nnz, ix->mode[0].cap, &yb, &gb, &pb);
   b.gram = reinterpret_cast<double*>(base + yb);
@@ -716,10 +885,13 @@ static vest_status core_grams(const vest_index* ix, const DevModel<T>& M, const 
                               cudaStream_t s) {
   const DevMode<T> csr = dev_mode<T>(ix, 0);
   const int64_t ntasks = ceil_div(ix->nnz, kCoreTask);
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntasks, (int64_t)num_sms() * 4));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ntasks, 8), (int64_t)num_sms() * 2));
+  // every gram pass writes the same slots (one per row piece): clear them once
+  VEST_CUDA(cudaMemsetAsync(bf.srow, 0xFF, (size_t)c.slots * 4, s));
+  bool have_x = false;
   for (int qc = 0; qc < c.nq0; ++qc) {
     const int q0 = qc * c.m, mq = std::min(c.m, c.J1 - q0), nY = mq * (mq + 1) / 2;
-    const int Sg = (int)std::max<int64_t>(1, std::min<int64_t>(c.S, kGramMaxP / nY));
+    const int Sg = c.SgMax;
     for (int64_t s0 = 0; s0 < c.S; s0 += Sg) {
       const int sg = (int)std::min<int64_t>(Sg, c.S - s0);
       GramArgs ga{};
@@ -731,29 +903,35 @@ static vest_status core_grams(const vest_index* ix, const DevModel<T>& M, const 
       ga.s0 = s0;
       ga.Sg = sg;
       ga.P = sg * nY;
-      ga.kmax = kmax_for<T>(ga.P);
       ga.nnz = ix->nnz;
       ga.ntasks = ntasks;
       ga.Y = bf.Y;
       ga.srow = bf.srow;
-      VEST_CUDA(cudaMemsetAsync(bf.srow, 0xFF, (size_t)c.slots * 4, s));
       if (ix->nnz > 0) {
-        const size_t smem = smem_gram<T>(nY, sg, ga.P, ga.kmax);
+        const size_t smem = smem_gram<T>(mq, sg);
         auto kern = core_gram_pass_kernel<T>;
         VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<grid, kCoreTask, smem, s>>>(M, csr, ga);
+        kern<<<grid, 256, smem, s>>>(M, csr, ga);
         VEST_LAUNCH("core_gram_pass_kernel");
+      }
+      if (!have_x) {
+        core_gram_x_kernel<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(c.slots * c.nX, 256),
+                                                                                (int64_t)num_sms() * 8)),
+                                256, 0, s>>>(M, csr, bf.srow, c.slots, c.J0, c.nX, static_cast<T*>(bf.Xs));
+        VEST_LAUNCH("core_gram_x_kernel");
+        have_x = true;
       }
       GemmArgs gm{};
       gm.J0 = c.J0;
       gm.nX = c.nX;
       gm.P = ga.P;
       gm.nslots = c.slots;
+      gm.Xs = bf.Xs;
       gm.Y = bf.Y;
       gm.srow = bf.srow;
       gm.part = bf.part;
-      const dim3 gg((unsigned)(((c.nX + 31) / 32) * ((ga.P + 63) / 64)), kGramKSplit);
-      core_gram_gemm_kernel<T><<<gg, 256, 0, s>>>(M, csr, gm);
+      const dim3 gg((unsigned)(((c.nX + 63) / 64) * ((ga.P + 63) / 64)), kGramKSplit);
+      core_gram_gemm_kernel<T><<<gg, 256, 0, s>>>(gm);
       VEST_LAUNCH("core_gram_gemm_kernel");
       const int b = c.J0 * mq, nm = b * (b + 1) / 2;
       for (int si = 0; si < sg; ++si) {
@@ -786,8 +964,18 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
   a.J1 = c.J1;
   a.nnz = ix->nnz;
   a.part = bf.part;
-  T* U = reinterpret_cast<T*>(bf.Y);  // the per-piece gram region is free again: u per row
+  // the per-piece gram region is free again: u and the a0 row per non-empty row
+  T* U = reinterpret_cast<T*>(bf.Y);
+  T* A0c = U + (size_t)(ix->mode[0].cap + 1) * kCoreMaxM;
   const int nctas_g = kCorePassCtas;
+  const size_t gsm = (size_t)8 * 32 * c.J0 * sizeof(T);
+  if (ix->nnz > 0) {
+    core_a0c_kernel<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->mode[0].cap * c.J0, 256),
+                                                                         num_sms() * 8)),
+                         256, 0, s>>>(M, csr.nzrow, csr.nnzrows, c.J0, A0c);
+    VEST_LAUNCH("core_a0c_kernel");
+    VEST_CUDA(cudaFuncSetAttribute(core_g_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+  }
   int64_t iblk = 0;
   for (int64_t sfx = 0; sfx < c.S; ++sfx) {
     for (int qc = 0; qc < c.nq0; ++qc, ++iblk) {
@@ -802,7 +990,7 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
                              256, 0, s>>>(M, csr.nzrow, csr.nnzrows, dbuf[(iblk + 1) & 1], c.J0, a.prev.m, U);
           VEST_LAUNCH("core_u_kernel");
         }
-        core_g_pass_kernel<T><<<nctas_g, 256, 0, s>>>(M, csr, r0, U, a);
+        core_g_pass_kernel<T><<<nctas_g, 256, gsm, s>>>(M, csr, r0, U, A0c, a);
         VEST_LAUNCH("core_g_pass_kernel");
         core_vec_merge_kernel<<<(unsigned)ceil_div(blk.b, 32), 256, 0, s>>>(bf.part, nctas_g, blk.b, gvec);
         VEST_LAUNCH("core_vec_merge_kernel");
@@ -830,7 +1018,6 @@ vest_status core_responsibility(const vest_index* ix, const vest_model* mdl, con
   const CoreBufs bf = core_bufs(ix, mdl, scratch, plan);
   const DevMode<T> csr = dev_mode<T>(ix, 0);
   const int64_t ntasks = ceil_div(ix->nnz, kCoreTask);
-  const int nctas = (int)std::max<int64_t>(1, std::min<int64_t>(ntasks, kCorePassCtas));
   double* sums = bf.gram;  // reuse the gram region: [2 * J0 * SJ]
   for (int64_t s0 = 0; s0 < c.S; s0 += c.SgStats) {
     StatsArgs a{};
@@ -839,18 +1026,22 @@ vest_status core_responsibility(const vest_index* ix, const vest_model* mdl, con
     a.s0 = s0;
     a.Sg = (int)std::min<int64_t>(c.SgStats, c.S - s0);
     a.SJ = a.Sg * c.J1;
-    a.P = 2 * a.SJ;
-    a.kmax = kmax_for<T>(a.P);
     a.nnz = ix->nnz;
     a.ntasks = ntasks;
     a.part = bf.part;
     const int nacc = 2 * c.J0 * a.SJ;
     if (ix->nnz > 0) {
-      const size_t smem = smem_stats<T>(c.J0, a.SJ, a.P, a.kmax);
-      auto kern = core_stats_kernel<T>;
-      VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      kern<<<nctas, kCoreTask, smem, s>>>(M, csr, resid_csr0, a);
-      VEST_LAUNCH("core_stats_kernel");
+      const int nwarps = stats_warps<T>(c.J0, c.J1, a.Sg, a.SJ);
+      const int nctas = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ntasks, nwarps), kCorePassCtas));
+      const size_t smem = smem_stats<T>(c.J0, c.J1, a.Sg, a.SJ, nwarps, &a.red_off);
+      switch (jn_bucket(c.J0)) {
+        case 4: VEST_TRY(launch_stats<T, 4>(M, csr, resid_csr0, a, nctas, nwarps, smem, s)); break;
+        case 8: VEST_TRY(launch_stats<T, 8>(M, csr, resid_csr0, a, nctas, nwarps, smem, s)); break;
+        case 10: VEST_TRY(launch_stats<T, 10>(M, csr, resid_csr0, a, nctas, nwarps, smem, s)); break;
+        case 12: VEST_TRY(launch_stats<T, 12>(M, csr, resid_csr0, a, nctas, nwarps, smem, s)); break;
+        case 16: VEST_TRY(launch_stats<T, 16>(M, csr, resid_csr0, a, nctas, nwarps, smem, s)); break;
+        default: VEST_TRY(launch_stats<T, 32>(M, csr, resid_csr0, a, nctas, nwarps, smem, s)); break;
+      }
       core_vec_merge_kernel<<<(unsigned)ceil_div(nacc, 32), 256, 0, s>>>(bf.part, nctas, nacc, sums);
       VEST_LAUNCH("core_vec_merge_kernel");
     } else {
