@@ -127,6 +127,13 @@ ScratchPlan plan_scratch(const vest_index* ix, const vest_model* m) {
   size_t yb, gb, cpb;
   const int64_t cap0 = std::min<int64_t>(ix->dims[0], std::max<int64_t>(ix->nnz, 1));
   p.off_core = o; o += align_up(core_scratch_bytes(m, ix->nnz, cap0, &yb, &gb, &cpb));
+  size_t rb = 0;  // the update's outputs per row (J + J(J+1)/2) exceed the responsibility's (2J)
+  for (int n = 0; n < m->order; ++n) {
+    const int64_t capn = std::min<int64_t>(ix->dims[n], std::max<int64_t>(ix->nnz, 1));
+    const int J = m->ranks[n];
+    rb = std::max(rb, (size_t)capn * (size_t)(J + J * (J + 1) / 2) * 8);
+  }
+  p.off_rowbuf = o; p.rowbuf_bytes = align_up(rb); o += p.rowbuf_bytes;
   p.total = o;
   return p;
 }

@@ -110,7 +110,7 @@ __device__ __forceinline__ void suffix_weights(const DevModel<T>& M, const int32
 }
 
 // ================================================================== gram pass
-constexpr int kGramSgB = 16;  // suffixes per gram group (registers per lane: 2 x kGramSgB)
+constexpr int kGramSgB = 16;  // suffixes per gram group at most (registers per lane: 2 x 16)
 
 struct GramArgs {
   int J0, J1;
@@ -126,18 +126,19 @@ struct GramArgs {
 // piece (the part of a mode-0 row inside one 256-entry task, slot = row + task)
 //   Y(s, q, q') = sum over the piece of c(s)^2 a1[q0 + q] a1[q0 + q'],  q <= q',
 // stored at Y[slot][s * nY + packed(q, q')].  Each warp takes whole tasks (warp-strided) and
-// walks them 32 entries at a time: the lanes stage one entry each (row, c(s)^2 of the group,
-// the a1 values of the chunk); then every lane runs through the entries in order for its
-// pairs (q, q') = packed index lane, lane + 32 and all Sg suffixes, and writes the piece's
-// sums at a row change and at the end of the task.
-template <typename T>
+// walks them 32 entries at a time: the lanes stage one entry each (row, c(s)^2 of the group
+// zero-padded to SGB, the a1 values of the chunk); then every lane runs through the entries
+// in order for its pairs (q, q') = packed index lane, lane + 32 and all SGB >= Sg suffixes
+// (the padding adds zeros), and writes the piece's sums at a row change and at the end of
+// the task.
+template <typename T, int SGB>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) core_gram_pass_kernel(DevModel<T> M, DevMode<T> csr, GramArgs a) {
   constexpr int V = 16 / (int)sizeof(T);  // values per 16-byte shared-memory load
+  static_assert(SGB % V == 0, "SGB must fill whole 16-byte loads");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int mq = a.mq, nY = a.nY, Sg = a.Sg, P = a.P;
-  const int sgp = (Sg + V - 1) / V * V;            // c(s)^2 padded to whole 16-byte loads
-  const int ld = (sgp + mq + V - 1) / V * V;       // staged entry: c(s)^2, a1 chunk
+  const int ld = (SGB + mq + V - 1) / V * V;  // staged entry: c(s)^2 (SGB), a1 chunk
   T* st = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * ld;
   int* sk = reinterpret_cast<int*>(reinterpret_cast<T*>(smem_raw) + (size_t)nwarps * 32 * ld) + warp * 32;
   T* Y = static_cast<T*>(a.Y);
@@ -152,7 +153,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) core_gram_pass_ke
     qa[i] = x;
     qb[i] = y;
   }
-  T acc[2][kGramSgB];
+  T acc[2][SGB];
+  auto flush = [&](int64_t slot, int row) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+      if (on[i])
+#pragma unroll
+        for (int s = 0; s < SGB; ++s)
+          if (s < Sg) Y[slot * P + s * nY + lane + 32 * i] = acc[i][s];
+    if (lane == 0) a.srow[slot] = row;
+  };
   const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw = (int64_t)gridDim.x * nwarps;
   for (int64_t task = gw; task < a.ntasks; task += nw) {
     const int64_t t0 = task * kCoreTask, t1 = min(t0 + (int64_t)kCoreTask, a.nnz);
@@ -165,9 +175,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) core_gram_pass_ke
         T* se = st + lane * ld;
         suffix_weights<T>(M, csr.oidx, a.nnz, p, a.s0, Sg, se, 1);
         for (int s = 0; s < Sg; ++s) se[s] *= se[s];
-        for (int s = Sg; s < sgp; ++s) se[s] = T(0);
+        for (int s = Sg; s < SGB; ++s) se[s] = T(0);
         const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * a.J1 + a.q0;
-        for (int q = 0; q < mq; ++q) se[sgp + q] = a1[q];
+        for (int q = 0; q < mq; ++q) se[SGB + q] = a1[q];
       }
       __syncwarp();
       const int n = (int)min((int64_t)32, t1 - c0);
@@ -175,63 +185,37 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) core_gram_pass_ke
         const int k = sk[e];
         const T* se = st + e * ld;
         if (k != cur) {
-          if (cur >= 0) {
-            const int64_t slot = cur + task;
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-              if (on[i])
-#pragma unroll
-                for (int s = 0; s < kGramSgB; ++s)
-                  if (s < Sg) Y[slot * P + s * nY + lane + 32 * i] = acc[i][s];
-            if (lane == 0) a.srow[slot] = cur;
-          }
+          if (cur >= 0) flush(cur + task, cur);
           cur = k;
 #pragma unroll
           for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int s = 0; s < kGramSgB; ++s) acc[i][s] = T(0);
+            for (int s = 0; s < SGB; ++s) acc[i][s] = T(0);
         }
-        T cv[kGramSgB];
+        T cv[SGB];
 #pragma unroll
-        for (int s4 = 0; s4 < kGramSgB; s4 += V) {
-          if (s4 < Sg) {
-            if constexpr (sizeof(T) == 4) {
-              const float4 v = *reinterpret_cast<const float4*>(se + s4);
-              cv[s4] = v.x;
-              cv[s4 + 1] = v.y;
-              cv[s4 + 2] = v.z;
-              cv[s4 + 3] = v.w;
-            } else {
-              const double2 v = *reinterpret_cast<const double2*>(se + s4);
-              cv[s4] = v.x;
-              cv[s4 + 1] = v.y;
-            }
+        for (int s4 = 0; s4 < SGB; s4 += V) {
+          if constexpr (sizeof(T) == 4) {
+            const float4 v = *reinterpret_cast<const float4*>(se + s4);
+            cv[s4] = v.x;
+            cv[s4 + 1] = v.y;
+            cv[s4 + 2] = v.z;
+            cv[s4 + 3] = v.w;
           } else {
-#pragma unroll
-            for (int u = 0; u < V; ++u) cv[s4 + u] = T(0);
+            const double2 v = *reinterpret_cast<const double2*>(se + s4);
+            cv[s4] = v.x;
+            cv[s4 + 1] = v.y;
           }
         }
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-          if (on[i]) {
-            const T kq = se[sgp + qa[i]] * se[sgp + qb[i]];
+          const T kq = se[SGB + qa[i]] * se[SGB + qb[i]];
 #pragma unroll
-            for (int s = 0; s < kGramSgB; ++s)
-              if (s < Sg) acc[i][s] += cv[s] * kq;
-          }
+          for (int s = 0; s < SGB; ++s) acc[i][s] += cv[s] * kq;
         }
       }
     }
-    if (cur >= 0) {
-      const int64_t slot = cur + task;
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-        if (on[i])
-#pragma unroll
-          for (int s = 0; s < kGramSgB; ++s)
-            if (s < Sg) Y[slot * P + s * nY + lane + 32 * i] = acc[i][s];
-      if (lane == 0) a.srow[slot] = cur;
-    }
+    if (cur >= 0) flush(cur + task, cur);
   }
 }
 
@@ -422,10 +406,28 @@ __global__ void __launch_bounds__(256, 3) core_g_pass_kernel(DevModel<T> M, DevM
   for (int i = 0; i < kPer; ++i) as[i] = ac[i] = T(0);
   const int64_t nchunks = ceil_div(a.nnz, 32);
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp, nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  // the coalesced loads of a chunk (row, mode-1 index, mode-2 index when N = 3, r) are
+  // issued one chunk ahead
+  const bool n3 = M.N == 3;
+  int nk = 0, ni1 = 0, ni2 = 0;
+  T nrv = T(0);
+  auto prefetch = [&](int64_t ch) {
+    const int64_t p = ch * 32 + lane;
+    if (ch < nchunks && p < a.nnz) {
+      nk = csr.rowk[p];
+      ni1 = csr.oidx[p];
+      if (n3) ni2 = csr.oidx[a.nnz + p];
+      nrv = r[p];
+    }
+  };
+  prefetch(gw);
   for (int64_t ch = gw; ch < nchunks; ch += nw) {
     const int64_t p = ch * 32 + lane;
     const bool valid = p < a.nnz;
-    const int k = valid ? csr.rowk[p] : -1 - lane;
+    const int k = valid ? nk : -1 - lane;
+    const int i1 = ni1, i2 = ni2;
+    const T rv0 = nrv;
+    prefetch(ch + nw);
     const int kup = __shfl_up_sync(0xffffffffu, k, 1);
     const bool head = valid && (lane == 0 || kup != k);
     T h[kCoreMaxM];
@@ -437,15 +439,16 @@ __global__ void __launch_bounds__(256, 3) core_g_pass_kernel(DevModel<T> M, DevM
       for (int j = 0; j < J0; ++j) sa[lane * J0 + j] = a0[j];
     }
     if (valid) {
-      const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * a.J1;
-      T rv = r[p];
+      const T* a1 = M.A[1] + (int64_t)i1 * a.J1;
+      T rv = rv0;
       T v[kCoreMaxM];
 #pragma unroll
       for (int q = 0; q < kCoreMaxM; ++q)
         if (q < m) v[q] = a1[a.cur.q0 + q];
       if (a.has_prev) {
         T cp;
-        suffix_weights<T>(M, csr.oidx, a.nnz, p, a.prev.s, 1, &cp, 1);
+        if (n3) cp = M.A[2][(int64_t)i2 * M.J[2] + a.prev.s];
+        else suffix_weights<T>(M, csr.oidx, a.nnz, p, a.prev.s, 1, &cp, 1);
         const T* u = U + (int64_t)k * kCoreMaxM;
         T acc = T(0);
 #pragma unroll
@@ -455,7 +458,8 @@ __global__ void __launch_bounds__(256, 3) core_g_pass_kernel(DevModel<T> M, DevM
         r[p] = rv;
       }
       T c;
-      suffix_weights<T>(M, csr.oidx, a.nnz, p, a.cur.s, 1, &c, 1);
+      if (n3) c = M.A[2][(int64_t)i2 * M.J[2] + a.cur.s];
+      else suffix_weights<T>(M, csr.oidx, a.nnz, p, a.cur.s, 1, &c, 1);
       const T rc = rv * c;
 #pragma unroll
       for (int q = 0; q < kCoreMaxM; ++q)
@@ -619,7 +623,7 @@ __host__ __device__ inline size_t stats_run_elems(int J0, int spl) { return (siz
 // one partial per CTA.
 template <typename T, int J0B>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
-    core_stats_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ r, StatsArgs a) {
+    core_stats_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ r, const T* __restrict__ A0c, StatsArgs a) {
   constexpr int SPL = stats_spl(J0B);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -647,6 +651,20 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
   T a0r[J0B];
   T h1[SPL], h2[SPL];
   const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw = (int64_t)gridDim.x * nwarps;
+  // the coalesced loads of a chunk (row, its position in A0c, mode-1 index, mode-2 index
+  // when N = 3, r) are issued one chunk ahead
+  const bool n3 = M.N == 3;
+  int nk = 0, ni1 = 0, ni2 = 0;
+  T nrv = T(0);
+  auto prefetch = [&](int64_t p) {
+    if (p >= 0 && p < a.nnz) {
+      nk = csr.rowk[p];
+      ni1 = csr.oidx[p];
+      if (n3) ni2 = csr.oidx[a.nnz + p];
+      nrv = r[p];
+    }
+  };
+  if (gw < a.ntasks) prefetch(gw * kCoreTask + lane);
   for (int64_t task = gw; task < a.ntasks; task += nw) {
     const int64_t t0 = task * kCoreTask, t1 = min(t0 + (int64_t)kCoreTask, a.nnz);
 #pragma unroll
@@ -656,17 +674,25 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
     int cur = -1;
     for (int64_t c0 = t0; c0 < t1; c0 += 32) {
       const int64_t p = c0 + lane;
+      const int k = nk, i1 = ni1, i2 = ni2;
+      const T rv = nrv;
+      // next chunk of this warp: the rest of the task, else the first chunk of its next task
+      prefetch(c0 + 32 < t1 ? c0 + 32 + lane : (task + nw < a.ntasks ? (task + nw) * kCoreTask + lane : -1));
       __syncwarp();
       if (p < t1) {
-        const int k = csr.rowk[p];
         sk[lane] = k;
         T* se = st + lane * ld;
-        const T* a0 = M.A[0] + (int64_t)csr.nzrow[k] * J0;
+        const T* a0 = A0c + (int64_t)k * J0;
         for (int j = 0; j < J0; ++j) se[j] = a0[j];
-        const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * J1;
+        const T* a1 = M.A[1] + (int64_t)i1 * J1;
         for (int q = 0; q < J1; ++q) se[J0 + q] = a1[q];
-        suffix_weights<T>(M, csr.oidx, a.nnz, p, a.s0, Sg, se + J0 + J1, 1);
-        se[J0 + J1 + Sg] = r[p];
+        if (n3) {
+          const T* a2 = M.A[2] + (int64_t)i2 * M.J[2] + a.s0;
+          for (int q = 0; q < Sg; ++q) se[J0 + J1 + q] = a2[q];
+        } else {
+          suffix_weights<T>(M, csr.oidx, a.nnz, p, a.s0, Sg, se + J0 + J1, 1);
+        }
+        se[J0 + J1 + Sg] = rv;
       }
       __syncwarp();
       const int n = (int)min((int64_t)32, t1 - c0);
@@ -815,11 +841,25 @@ size_t core_scratch_bytes(const vest_model* m, int64_t nnz, int64_t cap0, size_t
   return *y_bytes + *gram_bytes + *part_bytes;
 }
 
+// Suffix slots per lane and pair in the gram pass: the smallest of 4, 8, 12, 16 that holds Sg.
+static int gram_sgb(int Sg) { return Sg <= 4 ? 4 : Sg <= 8 ? 8 : Sg <= 12 ? 12 : 16; }
+
 template <typename T>
-static size_t smem_gram(int mq, int Sg) {
+static size_t smem_gram(int mq, int sgb) {
   const int V = 16 / (int)sizeof(T);
-  const int sgp = (Sg + V - 1) / V * V, ld = (sgp + mq + V - 1) / V * V;
+  const int ld = (sgb + mq + V - 1) / V * V;
   return (size_t)8 * 32 * ld * sizeof(T) + (size_t)8 * 32 * 4;
+}
+
+template <typename T, int SGB>
+static vest_status launch_gram(const DevModel<T>& M, const DevMode<T>& csr, const GramArgs& ga, int grid,
+                               cudaStream_t s) {
+  const size_t smem = smem_gram<T>(ga.mq, SGB);
+  auto kern = core_gram_pass_kernel<T, SGB>;
+  VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, 256, smem, s>>>(M, csr, ga);
+  VEST_LAUNCH("core_gram_pass_kernel");
+  return VEST_OK;
 }
 
 // Shared memory of the stats pass; *red_off receives the offset of the FP64 warp
@@ -844,11 +884,11 @@ static int stats_warps(int J0, int J1, int Sg, int SJ) {
 }
 
 template <typename T, int J0B>
-static vest_status launch_stats(const DevModel<T>& M, const DevMode<T>& csr, const T* r, const StatsArgs& a, int grid,
-                                int nwarps, size_t smem, cudaStream_t s) {
+static vest_status launch_stats(const DevModel<T>& M, const DevMode<T>& csr, const T* r, const T* A0c,
+                                const StatsArgs& a, int grid, int nwarps, size_t smem, cudaStream_t s) {
   auto kern = core_stats_kernel<T, J0B>;
   VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, 32 * nwarps, smem, s>>>(M, csr, r, a);
+  kern<<<grid, 32 * nwarps, smem, s>>>(M, csr, r, A0c, a);
   VEST_LAUNCH("core_stats_kernel");
   return VEST_OK;
 }
@@ -908,11 +948,12 @@ static vest_status core_grams(const vest_index* ix, const DevModel<T>& M, const 
       ga.Y = bf.Y;
       ga.srow = bf.srow;
       if (ix->nnz > 0) {
-        const size_t smem = smem_gram<T>(mq, sg);
-        auto kern = core_gram_pass_kernel<T>;
-        VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<grid, 256, smem, s>>>(M, csr, ga);
-        VEST_LAUNCH("core_gram_pass_kernel");
+        switch (gram_sgb(sg)) {
+          case 4: VEST_TRY((launch_gram<T, 4>(M, csr, ga, grid, s))); break;
+          case 8: VEST_TRY((launch_gram<T, 8>(M, csr, ga, grid, s))); break;
+          case 12: VEST_TRY((launch_gram<T, 12>(M, csr, ga, grid, s))); break;
+          default: VEST_TRY((launch_gram<T, 16>(M, csr, ga, grid, s))); break;
+        }
       }
       if (!have_x) {
         core_gram_x_kernel<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(c.slots * c.nX, 256),
@@ -1019,6 +1060,13 @@ vest_status core_responsibility(const vest_index* ix, const vest_model* mdl, con
   const DevMode<T> csr = dev_mode<T>(ix, 0);
   const int64_t ntasks = ceil_div(ix->nnz, kCoreTask);
   double* sums = bf.gram;  // reuse the gram region: [2 * J0 * SJ]
+  T* A0c = reinterpret_cast<T*>(bf.Y);  // the per-piece gram region is free here: a0 per non-empty row
+  if (ix->nnz > 0) {
+    core_a0c_kernel<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->mode[0].cap * c.J0, 256),
+                                                                         num_sms() * 8)),
+                         256, 0, s>>>(M, csr.nzrow, csr.nnzrows, c.J0, A0c);
+    VEST_LAUNCH("core_a0c_kernel");
+  }
   for (int64_t s0 = 0; s0 < c.S; s0 += c.SgStats) {
     StatsArgs a{};
     a.J0 = c.J0;
@@ -1035,12 +1083,12 @@ vest_status core_responsibility(const vest_index* ix, const vest_model* mdl, con
       const int nctas = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ntasks, nwarps), kCorePassCtas));
       const size_t smem = smem_stats<T>(c.J0, c.J1, a.Sg, a.SJ, nwarps, &a.red_off);
       switch (jn_bucket(c.J0)) {
-        case 4: VEST_TRY(launch_stats<T, 4>(M, csr, resid_csr0, a, nctas, nwarps, smem, s)); break;
-        case 8: VEST_TRY(launch_stats<T, 8>(M, csr, resid_csr0, a, nctas, nwarps, smem, s)); break;
-        case 10: VEST_TRY(launch_stats<T, 10>(M, csr, resid_csr0, a, nctas, nwarps, smem, s)); break;
-        case 12: VEST_TRY(launch_stats<T, 12>(M, csr, resid_csr0, a, nctas, nwarps, smem, s)); break;
-        case 16: VEST_TRY(launch_stats<T, 16>(M, csr, resid_csr0, a, nctas, nwarps, smem, s)); break;
-        default: VEST_TRY(launch_stats<T, 32>(M, csr, resid_csr0, a, nctas, nwarps, smem, s)); break;
+        case 4: VEST_TRY(launch_stats<T, 4>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
+        case 8: VEST_TRY(launch_stats<T, 8>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
+        case 10: VEST_TRY(launch_stats<T, 10>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
+        case 12: VEST_TRY(launch_stats<T, 12>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
+        case 16: VEST_TRY(launch_stats<T, 16>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
+        default: VEST_TRY(launch_stats<T, 32>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
       }
       core_vec_merge_kernel<<<(unsigned)ceil_div(nacc, 32), 256, 0, s>>>(bf.part, nctas, nacc, sums);
       VEST_LAUNCH("core_vec_merge_kernel");

@@ -10,13 +10,15 @@
 //            responsibility, per row piece (accumulator: T): short pieces one
 //            warp each, long pieces cut into 32-entry chunks over all warps and
 //            combined in chunk order; at most KMAX pieces per round;
-//   phase 3  one thread per row: rows that lie inside the task are finished
-//            at once (sequential CD over j, FP64); a row cut by a task edge
-//            writes its piece to a spill slot, and the task where the row
-//            starts registers it for the fix-up kernel, which adds the pieces
-//            in task order in FP64 and finishes the row.
-// Rows of A^(n) are independent (delta does not involve A^(n)), so finishing
-// them while other tasks run is safe.
+//   phase 3  one thread per row: a row that ends inside the block's task range
+//            stores its sums (FP64) in the row buffer; a row cut by the edges of
+//            the range writes its piece to a spill slot, and the block where the
+//            row starts registers it for the fix-up kernel, which adds the
+//            pieces in block order in FP64 and stores the sums likewise.
+// A last kernel finishes every non-empty row from the row buffer, one thread
+// per row (sequential CD over j in FP64), so the FP64 work runs in full warps
+// instead of one lane per row inside the task kernel.  Rows of A^(n) are
+// independent (delta does not involve A^(n)), so the order is free.
 #include <algorithm>
 
 #include "delta.cuh"
@@ -38,6 +40,7 @@ struct SweepArgs {
   const uint8_t* onz;
   double* spill;       // [ntasks][2][P]
   int32_t* spanning;   // [ntasks]
+  double* rowbuf;      // [non-empty rows][P]: the FP64 sums of every row
   // responsibility
   const void* resid_coo;
   const double* stats;  // device {.., x_norm2 at [1], .., RE at [4]}
@@ -140,7 +143,6 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
     for (int64_t e = threadIdx.x; e < core_elems; e += blockDim.x) sG[e] = gcore[e];
     g = sG;
   }
-  const int n = r.n;
   const int Jn = r.Jn;
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     if (p < Jn) {
@@ -212,13 +214,16 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
         const bool continues = re > t1;
         const bool started_here = rs >= rt0;
         if (!continues && !carried_in && rs >= t0) {
-          finish_row<T, T, MODE>(M, n, (int64_t)csr.nzrow[k0 + k], piece, a);
+          double* dst = a.rowbuf + (size_t)(k0 + k) * P;
+          for (int i = 0; i < P; ++i) dst[i] = (double)piece[i];
         } else {
           double* acc = continues ? cout : cin;
           for (int i = 0; i < P; ++i) acc[i] = (double)piece[i] + (carried_in ? cin[i] : 0.0);
           if (!continues) {
-            if (started_here) finish_row<T, double, MODE>(M, n, (int64_t)csr.nzrow[k0 + k], acc, a);
-            else {  // the row entered the block's range from an earlier block: incoming partial
+            if (started_here) {
+              double* dst = a.rowbuf + (size_t)(k0 + k) * P;
+              for (int i = 0; i < P; ++i) dst[i] = acc[i];
+            } else {  // the row entered the block's range from an earlier block: incoming partial
               double* sp = a.spill + ((size_t)blockIdx.x * 2 + 0) * P;
               for (int i = 0; i < P; ++i) sp[i] = acc[i];
             }
@@ -271,16 +276,21 @@ __global__ void __launch_bounds__(256) sweep_fixup_kernel(DevModel<T> M, DevMode
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int pp = 0; pp < P; ++pp) {
-        double acc = 0.0;
-        for (int gg = 0; gg < groups; ++gg) acc += part[gg * P + pp];
-        part[pp] = acc;
-      }
-      finish_row<T, double, MODE>(M, a.r.n, (int64_t)csr.nzrow[kg], part, a);
+    for (int pp = threadIdx.x; pp < P; pp += blockDim.x) {
+      double acc = 0.0;
+      for (int gg = 0; gg < groups; ++gg) acc += part[gg * P + pp];
+      a.rowbuf[(size_t)kg * P + pp] = acc;
     }
     __syncthreads();
   }
+}
+
+// Every non-empty row from its FP64 sums in the row buffer, one thread per row.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(128) finish_rows_kernel(DevModel<T> M, DevMode<T> csr, SweepArgs a) {
+  const int64_t R = *csr.nnzrows;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < R; k += (int64_t)gridDim.x * blockDim.x)
+    finish_row<T, double, MODE>(M, a.r.n, (int64_t)csr.nzrow[k], a.rowbuf + (size_t)k * a.P, a);
 }
 
 // Rows with no observed entry: the update gives 0; their Delta is 0.
@@ -410,6 +420,8 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
   if ((size_t)nblocks * 2 * a.P * 8 > plan.spill_bytes || nblocks > plan.ntasks)
     return fail(VEST_ERR_WORKSPACE, "scratch spill region too small");
   a.spill = reinterpret_cast<double*>(scratch + plan.off_spill);
+  if ((size_t)ix->mode[n].cap * a.P * 8 > plan.rowbuf_bytes) return fail(VEST_ERR_WORKSPACE, "scratch row buffer too small");
+  a.rowbuf = reinterpret_cast<double*>(scratch + plan.off_rowbuf);
   a.spanning = reinterpret_cast<int32_t*>(scratch + plan.off_spanning);
   const DevMode<T> csr = dev_mode<T>(ix, n);
   const int eg = std::max(1, std::min<int>((int)ceil_div(M.I[n], 256), num_sms() * 8));
@@ -424,6 +436,9 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
   const int64_t fgrid = std::min<int64_t>(nblocks, (int64_t)num_sms() * 8);
   fk<<<(unsigned)fgrid, 256, fsmem, s>>>(M, csr, a, (int)nblocks);
   VEST_LAUNCH("sweep_fixup_kernel");
+  const int64_t rgrid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->mode[n].cap, 128), (int64_t)num_sms() * 8));
+  finish_rows_kernel<T, MODE><<<(unsigned)rgrid, 128, 0, s>>>(M, csr, a);
+  VEST_LAUNCH("finish_rows_kernel");
   return VEST_OK;
 }
 

@@ -138,7 +138,8 @@ struct ScratchPlan {
   size_t off_status, off_gperm, off_spill, off_spanning, off_resid, off_resid_coo, off_part, off_small;
   size_t off_prune_keys, off_prune_vals, off_prune_tmp;
   size_t off_core;  // core-sweep region: per-piece gram statistics, block Grams, partial sums
-  size_t gperm_bytes, spill_bytes, part_bytes;
+  size_t off_rowbuf;  // factor sweep: FP64 sums of every non-empty row of one mode
+  size_t gperm_bytes, spill_bytes, part_bytes, rowbuf_bytes;
   int task;        // alpha per task in the factor sweep
   int64_t ntasks;  // factor-sweep tasks per mode
 };
