@@ -11,10 +11,12 @@
 //            warp each, long pieces cut into 32-entry chunks over all warps and
 //            combined in chunk order; at most KMAX pieces per round;
 //   phase 3  one thread per row: a row that ends inside the block's task range
-//            stores its sums (FP64) in the row buffer; a row cut by the edges of
-//            the range writes its piece to a spill slot, and the block where the
-//            row starts registers it for the fix-up kernel, which adds the
-//            pieces in block order in FP64 and stores the sums likewise.
+//            stores its sums in the row buffer (a row cut by task edges inside
+//            the range is carried from task to task with Kahan compensation);
+//            a row cut by the edges of the range writes its piece to a spill
+//            slot, and the block where the row starts registers it for the
+//            fix-up kernel, which adds the pieces in block order in FP64 and
+//            stores the sums likewise.
 // A last kernel finishes every non-empty row from the row buffer, one thread
 // per row (sequential CD over j in FP64), so the FP64 work runs in full warps
 // instead of one lane per row inside the task kernel.  Rows of A^(n) are
@@ -40,7 +42,9 @@ struct SweepArgs {
   const uint8_t* onz;
   double* spill;       // [ntasks][2][P]
   int32_t* spanning;   // [ntasks]
-  double* rowbuf;      // [non-empty rows][P]: the FP64 sums of every row
+  void* rowbuf;        // [non-empty rows][P]: the sums of every row, storage type
+  template <typename T>
+  __host__ __device__ T* rowbuf_t() const { return static_cast<T*>(rowbuf); }
   // responsibility
   const void* resid_coo;
   const double* stats;  // device {.., x_norm2 at [1], .., RE at [4]}
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
   int2* sTab = reinterpret_cast<int2*>(smem_raw + off);
   off += (size_t)P * sizeof(int2);
   off = (off + 15) & ~(size_t)15;
-  double* sCarry = reinterpret_cast<double*>(smem_raw + off);  // [2][P]: row sums carried to the next task
+  T* sCarry = reinterpret_cast<T*>(smem_raw + off);  // [2][sum, compensation][P]: row sums carried to the next task
   __shared__ PieceScratch pscr;
 
   const T* g = gcore;
@@ -170,8 +174,8 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
     const int cnt = (int)(t1 - t0);
     int64_t k0;
     const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, sptr, &k0);
-    double* cin = sCarry + (task & 1) * P;         // carried in from task - 1 (same block)
-    double* cout = sCarry + ((task + 1) & 1) * P;  // carried out to task + 1
+    T* cin = sCarry + (task & 1) * 2 * P;         // carried in from task - 1 (same block)
+    T* cout = sCarry + ((task + 1) & 1) * 2 * P;  // carried out to task + 1
 
     // phase 1: delta for the thread's E entries (threadIdx.x + e * blockDim.x)
     if ((int)threadIdx.x < cnt) {
@@ -204,8 +208,8 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
       const int nr = min(KMAX, nrows - r0);
       // phase 2: per-row sums over the task's pieces r0 .. r0 + nr - 1
       piece_sums<T>(sptr + r0, nr, t0, t1, P, sAcc, sPart, &pscr, f);
-      // phase 3: finish rows that end here; carry a row that continues into the
-      // block's next task; spill rows cut by the edges of the block's task range
+      // phase 3: store the sums of rows that end here; carry a row that continues into
+      // the block's next task; spill rows cut by the edges of the block's task range
       for (int kr = threadIdx.x; kr < nr; kr += blockDim.x) {
         const int k = r0 + kr;
         const int64_t rs = sptr[k], re = sptr[k + 1];
@@ -214,22 +218,30 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
         const bool continues = re > t1;
         const bool started_here = rs >= rt0;
         if (!continues && !carried_in && rs >= t0) {
-          double* dst = a.rowbuf + (size_t)(k0 + k) * P;
-          for (int i = 0; i < P; ++i) dst[i] = (double)piece[i];
+          T* dst = a.rowbuf_t<T>() + (size_t)(k0 + k) * P;
+          for (int i = 0; i < P; ++i) dst[i] = piece[i];
         } else {
-          double* acc = continues ? cout : cin;
-          for (int i = 0; i < P; ++i) acc[i] = (double)piece[i] + (carried_in ? cin[i] : 0.0);
+          // running sums of a row cut by task edges: (sum, compensation) in T
+          T* as = continues ? cout : cin;
+          T* ac = as + P;
+          for (int i = 0; i < P; ++i) {
+            T sum = carried_in ? cin[i] : T(0), cmp = carried_in ? cin[P + i] : T(0);
+            const T y = piece[i] - cmp;
+            const T t = sum + y;
+            ac[i] = (t - sum) - y;
+            as[i] = t;
+          }
           if (!continues) {
             if (started_here) {
-              double* dst = a.rowbuf + (size_t)(k0 + k) * P;
-              for (int i = 0; i < P; ++i) dst[i] = acc[i];
+              T* dst = a.rowbuf_t<T>() + (size_t)(k0 + k) * P;
+              for (int i = 0; i < P; ++i) dst[i] = as[i] - ac[i];
             } else {  // the row entered the block's range from an earlier block: incoming partial
               double* sp = a.spill + ((size_t)blockIdx.x * 2 + 0) * P;
-              for (int i = 0; i < P; ++i) sp[i] = acc[i];
+              for (int i = 0; i < P; ++i) sp[i] = (double)as[i] - (double)ac[i];
             }
           } else if (task + 1 == te) {  // leaves the block's range
             double* sp = a.spill + ((size_t)blockIdx.x * 2 + (started_here ? 1 : 0)) * P;
-            for (int i = 0; i < P; ++i) sp[i] = acc[i];
+            for (int i = 0; i < P; ++i) sp[i] = (double)as[i] - (double)ac[i];
             a.spanning[blockIdx.x] = started_here ? (int32_t)(k0 + k) : -1;
           }
         }
@@ -279,18 +291,18 @@ __global__ void __launch_bounds__(256) sweep_fixup_kernel(DevModel<T> M, DevMode
     for (int pp = threadIdx.x; pp < P; pp += blockDim.x) {
       double acc = 0.0;
       for (int gg = 0; gg < groups; ++gg) acc += part[gg * P + pp];
-      a.rowbuf[(size_t)kg * P + pp] = acc;
+      a.rowbuf_t<T>()[(size_t)kg * P + pp] = (T)acc;
     }
     __syncthreads();
   }
 }
 
-// Every non-empty row from its FP64 sums in the row buffer, one thread per row.
+// Every non-empty row from its sums in the row buffer, one thread per row (FP64 CD).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(128) finish_rows_kernel(DevModel<T> M, DevMode<T> csr, SweepArgs a) {
   const int64_t R = *csr.nnzrows;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < R; k += (int64_t)gridDim.x * blockDim.x)
-    finish_row<T, double, MODE>(M, a.r.n, (int64_t)csr.nzrow[k], a.rowbuf + (size_t)k * a.P, a);
+    finish_row<T, T, MODE>(M, a.r.n, (int64_t)csr.nzrow[k], a.rowbuf_t<T>() + (size_t)k * a.P, a);
 }
 
 // Rows with no observed entry: the update gives 0; their Delta is 0.
@@ -337,7 +349,7 @@ static size_t task_smem(int task, int kmax, int JN, int P, size_t core_bytes) {
   off += (size_t)kMaxLongPieces * P * sizeof(T);
   off += (size_t)P * sizeof(int2);
   off = (off + 15) & ~(size_t)15;
-  off += 2 * (size_t)P * sizeof(double);
+  off += 4 * (size_t)P * sizeof(T);
   return off;
 }
 
@@ -421,7 +433,7 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
     return fail(VEST_ERR_WORKSPACE, "scratch spill region too small");
   a.spill = reinterpret_cast<double*>(scratch + plan.off_spill);
   if ((size_t)ix->mode[n].cap * a.P * 8 > plan.rowbuf_bytes) return fail(VEST_ERR_WORKSPACE, "scratch row buffer too small");
-  a.rowbuf = reinterpret_cast<double*>(scratch + plan.off_rowbuf);
+  a.rowbuf = scratch + plan.off_rowbuf;
   a.spanning = reinterpret_cast<int32_t*>(scratch + plan.off_spanning);
   const DevMode<T> csr = dev_mode<T>(ix, n);
   const int eg = std::max(1, std::min<int>((int)ceil_div(M.I[n], 256), num_sms() * 8));
