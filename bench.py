@@ -173,6 +173,28 @@ def gpu_index_for_smi(local_rank: int) -> int:
     return local_rank
 
 
+# ------------------------------------------------------------------ replicas (weak scaling)
+def replica_seeds(w: datagen.Workload, rank: int):
+    """Every rank fits its own instance of the workload: data and init seeds offset by the rank."""
+    return w.data_seed + rank, w.init_seed + rank
+
+
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time: all ranks run the same steps, the job ends with the last."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(world: int, units_per_step: int, steps: int, ms: float) -> float:
+    """Units all ranks processed per second (each rank runs its own replica of the workload)."""
+    return world * units_per_step * steps / (ms / 1e3)
+
+
 def profiled_traffic(workload: str):
     """DRAM bytes per launch of the sweep task kernel from the committed ncu summary of this workload.
 
@@ -230,7 +252,8 @@ def main():
 
     w = datagen.WORKLOADS[args.workload]
     # every rank fits its own instance of the workload (weak scaling)
-    t, st, _ = datagen.make(w, data_seed=w.data_seed + rank, init_seed=w.init_seed + rank)
+    ds, iseed = replica_seeds(w, rank)
+    t, st, _ = datagen.make(w, data_seed=ds, init_seed=iseed)
     tdt = torch.float64 if w.dtype == "f64" else torch.float32
     reg = V.REG_LF if w.reg == "LF" else V.REG_L1
     ten = V.Tensor.from_host(t)
@@ -242,33 +265,38 @@ def main():
     units_per_step = N * nnz
 
     def step(model, index, evs=None):
-        # the factor sweep runs mode by mode (the same calls vest_sweep_factors(mode=-1) makes), so
-        # that each mode's sweep launch is timed on its own for the roofline
+        # one iteration of Algorithm 2: the factor sweep mode by mode (each mode's sweep timed on
+        # its own for the roofline), then the core sweep, loss, responsibility and prune in one call
         if evs:
             evs[0].record(stream)
         for n in range(N):
             V.vest_sweep_factors(index, model, reg, w.lam, n, sc)
             if evs:
                 evs[1 + n].record(stream)
-        V.vest_sweep_core(index, model, reg, w.lam, sc)
+        loss, _, _, _ = V.vest_iteration(index, model, reg, w.lam, PRUNE_RATE, sc, factor_sweep=False)
         if evs:
             evs[N + 1].record(stream)
-        loss = V.vest_loss(index, model, reg, w.lam, sc)
-        if evs:
-            evs[N + 2].record(stream)
-        df, dc, _, _ = V.vest_responsibility(index, model, sc, with_resp=False)
-        if evs:
-            evs[N + 3].record(stream)
-        V.vest_prune(model, df, dc, PRUNE_RATE, sc)
-        if evs:
-            evs[N + 4].record(stream)
         return loss
+
+    def step_separate(model, index, evs):
+        # the same iteration through the separate entry points, for the per-operation breakdown
+        evs[0].record(stream)
+        V.vest_sweep_factors(index, model, reg, w.lam, -1, sc)
+        evs[1].record(stream)
+        V.vest_sweep_core(index, model, reg, w.lam, sc)
+        evs[2].record(stream)
+        V.vest_loss(index, model, reg, w.lam, sc)
+        evs[3].record(stream)
+        df, dc, _, _ = V.vest_responsibility(index, model, sc, with_resp=False)
+        evs[4].record(stream)
+        V.vest_prune(model, df, dc, PRUNE_RATE, sc)
+        evs[5].record(stream)
 
     for _ in range(args.warmup):
         step(mdl, ix)
     torch.cuda.synchronize()
 
-    ops = [f"sweep_factors_mode{n}" for n in range(N)] + ["sweep_core", "loss", "responsibility", "prune"]
+    ops = [f"sweep_factors_mode{n}" for n in range(N)] + ["core_sweep+loss+responsibility+prune"]
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(ops) + 1)] for _ in range(args.steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(gpu_index_for_smi(local))
@@ -291,12 +319,18 @@ def main():
              for i, op in enumerate(ops)}
     mode_ms = [op_ms[f"sweep_factors_mode{n}"] for n in range(N)]
     op_ms["sweep_factors"] = sum(mode_ms)
-    if world > 1:
-        tt = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
-    value = world * units_per_step * args.steps / (elapsed_ms / 1e3)
+    elapsed_ms = max_over_ranks(elapsed_ms, world)
+    value = whole_job_rate(world, units_per_step, args.steps, elapsed_ms)
     final_loss = loss.cpu().numpy().tolist()
+
+    # per-operation breakdown through the separate entry points (after the timed region, on a copy)
+    sep_model = mdl.clone()
+    sep_evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    step_separate(sep_model, ix, sep_evs)
+    torch.cuda.synchronize()
+    sep_ms = {op: sep_evs[i].elapsed_time(sep_evs[i + 1])
+              for i, op in enumerate(["sweep_factors", "sweep_core", "loss", "responsibility", "prune"])}
+    del sep_model
 
     # ---------------- end to end: host buffers in, loss out, through the public API
     idx_h = torch.from_numpy(t.idx).pin_memory()
@@ -320,11 +354,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_wall))
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e_value = world * units_per_step * args.e2e_steps / (e2e_ms / 1e3) if args.e2e_steps > 0 else None
+    e2e_ms = max_over_ranks(e2e_ms, world)
+    e2e_value = whole_job_rate(world, units_per_step, args.e2e_steps, e2e_ms) if args.e2e_steps > 0 else None
 
     if rank != 0:
         if world > 1:
@@ -373,9 +404,11 @@ def main():
         "config": workload_config(w, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                                       "l2": "inputs larger than L2 (CSR per mode %.0f MB > 129 MB)" %
                                             ((N - 1) * 4 * nnz / 1e6 + s * nnz / 1e6),
-                                      "step": "factor sweep (all modes) + core sweep + loss + responsibility + "
-                                              "prune (pr=%g, the first pruning rate of Algorithm 2)" % PRUNE_RATE}),
+                                      "step": "one iteration of Algorithm 2: factor sweep (all modes) + core sweep + "
+                                              "loss + responsibility + prune (pr=%g, its first pruning rate)"
+                                              % PRUNE_RATE}),
         "op_ms": op_ms,
+        "separate_calls_ms": sep_ms,
         "sweep_only": {"value": world * units_per_step / (op_ms["sweep_factors"] / 1e3), "unit": UNIT},
         "final_loss": {"sq_err": final_loss[0], "objective": final_loss[3], "re": final_loss[4]},
         "roofline": roofline,

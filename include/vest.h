@@ -225,6 +225,23 @@ size_t vest_autosearch_scratch_bytes(const vest_index* ix, const vest_model* m);
 vest_status vest_autosearch(const vest_index* ix, vest_model* m, const vest_params* p, vest_report* report,
                             void* scratch, size_t scratch_bytes, void* stream);
 
+/* ---- a2-a8 in one call: one iteration of Algorithm 2 (lines 3-9): factor
+ * sweep over every mode (skipped when factor_sweep is 0, for callers that
+ * sweep the modes themselves), core sweep, loss of the swept model, and, when
+ * delta_factor is not NULL, the responsibility of every element (Eq. 5/6) and
+ * the prune with rate pr (count_mode as in vest_prune; pr = 0 prunes nothing).
+ * The residual that the core sweep keeps current serves the loss and the
+ * responsibility, so neither recomputes B: the results equal vest_sweep_factors
+ * (-1), vest_sweep_core, vest_loss, vest_responsibility and vest_prune in turn,
+ * up to rounding.  loss: device double[5] as in vest_loss, the model after the
+ * sweeps and before the prune.  delta_factor / delta_core: device outputs as in
+ * vest_responsibility (both NULL to stop after the loss).  n_pruned: NULL or
+ * device int64[order + 1] as in vest_prune.  scratch: vest_scratch_bytes().
+ * Never synchronises. */
+vest_status vest_iteration(const vest_index* ix, vest_model* m, int32_t reg, double lambda, double pr,
+                           int32_t count_mode, int32_t factor_sweep, double* loss, double* const* delta_factor,
+                           double* delta_core, int64_t* n_pruned, void* scratch, size_t scratch_bytes, void* stream);
+
 /* ---- vest_loss without a scratch buffer.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when they
  * need the loss, such as a host runtime that owns the device heap and forbids

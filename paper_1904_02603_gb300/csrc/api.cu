@@ -281,6 +281,42 @@ vest_status vest_responsibility(const vest_index* ix, const vest_model* m, doubl
   return core_responsibility<float>(ix, m, r0, stats, delta_core, resp_core, sc, plan, s);
 }
 
+vest_status vest_iteration(const vest_index* ix, vest_model* m, int32_t reg, double lambda, double pr,
+                           int32_t count_mode, int32_t factor_sweep, double* loss, double* const* delta_factor,
+                           double* delta_core, int64_t* n_pruned, void* scratch, size_t scratch_bytes, void* stream) {
+  VEST_TRY(check_pair(ix, m));
+  VEST_TRY(check_lambda(lambda));
+  if (reg != VEST_REG_LF && reg != VEST_REG_L1) return fail(VEST_ERR_INVALID, "unknown regulariser");
+  if (!loss) return fail(VEST_ERR_INVALID, "loss is NULL");
+  if (!(pr >= 0.0) || pr > 1.0) return fail(VEST_ERR_INVALID, "pr must be in [0, 1]");
+  const bool resp = delta_factor != nullptr;
+  if (resp != (delta_core != nullptr)) return fail(VEST_ERR_INVALID, "delta_factor and delta_core: both or neither");
+  if (resp)
+    for (int n = 0; n < m->order; ++n)
+      if (!delta_factor[n]) return fail(VEST_ERR_INVALID, "delta_factor entry is NULL");
+  ScratchPlan plan;
+  VEST_TRY(check_scratch(ix, m, scratch, scratch_bytes, &plan));
+  char* sc = static_cast<char*>(scratch);
+  const cudaStream_t s = as_stream(stream);
+  if (factor_sweep) VEST_TRY(vest_sweep_factors(ix, m, reg, lambda, -1, scratch, scratch_bytes, stream));
+  if (m->dtype == VEST_F64) {
+    VEST_TRY(sweep_core_impl<double>(ix, m, reg, lambda, sc, plan, s, loss));
+    if (!resp) return VEST_OK;
+    const double* r0 = reinterpret_cast<const double*>(sc + plan.off_resid);
+    VEST_TRY(responsibility_factors<double>(ix, m, loss, delta_factor, nullptr, sc, plan, s));
+    VEST_TRY(core_responsibility<double>(ix, m, r0, loss, delta_core, nullptr, sc, plan, s));
+  } else {
+    VEST_TRY(sweep_core_impl<float>(ix, m, reg, lambda, sc, plan, s, loss));
+    if (!resp) return VEST_OK;
+    const float* r0 = reinterpret_cast<const float*>(sc + plan.off_resid);
+    VEST_TRY(responsibility_factors<float>(ix, m, loss, delta_factor, nullptr, sc, plan, s));
+    VEST_TRY(core_responsibility<float>(ix, m, r0, loss, delta_core, nullptr, sc, plan, s));
+  }
+  if (m->dtype == VEST_F64)
+    return prune_impl<double>(m, delta_factor, delta_core, pr, count_mode, 0, 0.0, n_pruned, sc, plan, s);
+  return prune_impl<float>(m, delta_factor, delta_core, pr, count_mode, 0, 0.0, n_pruned, sc, plan, s);
+}
+
 static vest_status prune_checked(vest_model* m, double* const* delta_factor, const double* delta_core, double pr,
                                  int32_t count_mode, int32_t threshold_mode, double tau, int64_t* n_pruned, char* sc,
                                  const ScratchPlan& plan, cudaStream_t s) {

@@ -504,6 +504,90 @@ __global__ void __launch_bounds__(256, 3) core_g_pass_kernel(DevModel<T> M, DevM
   }
 }
 
+// After the last block: r -= c_last a1 . u(row) (the last block's change), the residual
+// copied to COO order, and per CTA (sum r^2, sum x^2) with per-thread Kahan sums in the
+// storage type, FP64 across threads.
+template <typename T>
+__global__ void __launch_bounds__(256) core_final_kernel(DevModel<T> M, DevMode<T> csr, T* __restrict__ r,
+                                                         T* __restrict__ rcoo, const T* __restrict__ U, CoreBlock last,
+                                                         double* __restrict__ part) {
+  __shared__ double red[32];
+  T sq = T(0), sqc = T(0), xx = T(0), xxc = T(0);
+  auto kadd = [](T& s, T& c, T v) {
+    const T y = v - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  };
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < csr.nnz; p += (int64_t)gridDim.x * blockDim.x) {
+    const int k = csr.rowk[p];
+    const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * M.J[1] + last.q0;
+    T cp;
+    suffix_weights<T>(M, csr.oidx, csr.nnz, p, last.s, 1, &cp, 1);
+    const T* u = U + (int64_t)k * kCoreMaxM;
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < kCoreMaxM; ++q)
+      if (q < last.m) acc += a1[q] * u[q];
+    const T rv = r[p] - cp * acc;
+    r[p] = rv;
+    rcoo[csr.perm[p]] = rv;
+    const T x = csr.val[p];
+    kadd(sq, sqc, rv * rv);
+    kadd(xx, xxc, x * x);
+  }
+  double v1 = (double)sq - (double)sqc, v2 = (double)xx - (double)xxc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+    v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[w] = v1;
+    red[16 + w] = v2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      a += red[i];
+      b += red[16 + i];
+    }
+    part[blockIdx.x * 2 + 0] = a;
+    part[blockIdx.x * 2 + 1] = b;
+  }
+}
+
+// First level of the FP64 merge of many per-CTA partials: block (x, g) sums the
+// partials c of group g (a contiguous range) for outputs 32 x .. 32 x + 31, eight
+// warps over c with four chains each, warps combined in order.
+constexpr int kMergeGroups = 16;
+
+__global__ void core_vec_merge1_kernel(const double* __restrict__ part, int nctas, int n, double* __restrict__ tmp) {
+  __shared__ double sh[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  const int per = (nctas + gridDim.y - 1) / gridDim.y;
+  const int c0 = blockIdx.y * per, c1 = min(nctas, c0 + per);
+  double c4[4] = {0, 0, 0, 0};
+  if (e < n) {
+    int c = c0 + w, u = 0;
+    for (; c + 24 < c1; c += 32) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) c4[k] += part[(size_t)(c + 8 * k) * n + e];
+    }
+    for (; c < c1; c += 8, ++u) c4[u & 3] += part[(size_t)c * n + e];
+  }
+  sh[w][lane] = (c4[0] + c4[1]) + (c4[2] + c4[3]);
+  __syncthreads();
+  if (w == 0 && e < n) {
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s += sh[k][lane];
+    tmp[(size_t)blockIdx.y * n + e] = s;
+  }
+}
+
 // out[e] = sum over c of part[c][e] in FP64: block of 8 warps x 32 outputs, warp w
 // sums c = w, w + 8, ... with four independent chains, warps combined in order.
 __global__ void core_vec_merge_kernel(const double* __restrict__ part, int nctas, int n, double* __restrict__ out) {
@@ -526,6 +610,18 @@ __global__ void core_vec_merge_kernel(const double* __restrict__ part, int nctas
     for (int k = 0; k < 8; ++k) s += sh[k][lane];
     out[e] = s;
   }
+}
+
+// sum over c < nctas of part[c][e] -> out[e], in two FP64 levels (groups of CTAs, then
+// the groups in order); tmp holds kMergeGroups x n doubles.
+static vest_status vec_merge(const double* part, int nctas, int n, double* out, double* tmp, cudaStream_t s) {
+  const int groups = std::max(1, std::min(kMergeGroups, nctas / 8));
+  const dim3 g1((unsigned)ceil_div(n, 32), (unsigned)groups);
+  core_vec_merge1_kernel<<<g1, 256, 0, s>>>(part, nctas, n, tmp);
+  VEST_LAUNCH("core_vec_merge1_kernel");
+  core_vec_merge_kernel<<<(unsigned)ceil_div(n, 32), 256, 0, s>>>(tmp, groups, n, out);
+  VEST_LAUNCH("core_vec_merge_kernel");
+  return VEST_OK;
 }
 
 // Exact sequential updates of one block (Eq. 12 / Eq. 14) by one warp: lane
@@ -628,7 +724,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int J0 = a.J0, J1 = a.J1, Sg = a.Sg, SJ = a.SJ;
-  const int ld = J0 + J1 + Sg + 1;  // staged entry: a0 row, a1 row, c(s), r
+  const int ld = J0 + J1 + Sg + 1;  // staged entry: a0 row (where a row starts), a1 row, c(s), r
   T* base = reinterpret_cast<T*>(smem_raw);
   const size_t stage = stats_stage_elems(J0, J1, Sg), run = stats_run_elems(J0, SPL);
   T* st = base + (size_t)warp * stage;
@@ -678,12 +774,16 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
       const T rv = nrv;
       // next chunk of this warp: the rest of the task, else the first chunk of its next task
       prefetch(c0 + 32 < t1 ? c0 + 32 + lane : (task + nw < a.ntasks ? (task + nw) * kCoreTask + lane : -1));
+      const int kup = __shfl_up_sync(0xffffffffu, k, 1);
       __syncwarp();
       if (p < t1) {
         sk[lane] = k;
         T* se = st + lane * ld;
-        const T* a0 = A0c + (int64_t)k * J0;
-        for (int j = 0; j < J0; ++j) se[j] = a0[j];
+        // a0 is read only where a row starts inside the chunk (and at lane 0)
+        if (lane == 0 || kup != k) {
+          const T* a0 = A0c + (int64_t)k * J0;
+          for (int j = 0; j < J0; ++j) se[j] = a0[j];
+        }
         const T* a1 = M.A[1] + (int64_t)i1 * J1;
         for (int q = 0; q < J1; ++q) se[J0 + q] = a1[q];
         if (n3) {
@@ -835,8 +935,8 @@ size_t core_scratch_bytes(const vest_model* m, int64_t nnz, int64_t cap0, size_t
   // the gram region also holds the responsibility sums (2 * J0 * SJ doubles)
   *gram_bytes = align_up(std::max((size_t)c.nblocks * c.nmmax, (size_t)2 * c.J0 * c.SJ) * 8);
   const size_t gemm = (size_t)kGramKSplit * c.nX * c.Pmax * 8;
-  const size_t gp = (size_t)kCorePassCtas * kCoreMaxB * 8;
-  const size_t st = (size_t)kCorePassCtas * 2 * c.J0 * c.SJ * 8;
+  const size_t gp = (size_t)(kCorePassCtas + kMergeGroups) * kCoreMaxB * 8;
+  const size_t st = (size_t)(kCorePassCtas + kMergeGroups) * 2 * c.J0 * c.SJ * 8;
   *part_bytes = align_up(std::max({gemm, gp, st}));
   return *y_bytes + *gram_bytes + *part_bytes;
 }
@@ -988,7 +1088,7 @@ static vest_status core_grams(const vest_index* ix, const DevModel<T>& M, const 
 
 template <typename T>
 vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg, double lambda, char* scratch,
-                            const ScratchPlan& plan, cudaStream_t s) {
+                            const ScratchPlan& plan, cudaStream_t s, double* final_loss) {
   const DevModel<T> M = dev_model<T>(mdl);
   if (M.N < 2) return fail(VEST_ERR_UNSUPPORTED, "order < 2");
   const CorePlan c = core_plan(M.J, M.N, ix->nnz, ix->mode[0].cap);
@@ -1033,8 +1133,7 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
         }
         core_g_pass_kernel<T><<<nctas_g, 256, gsm, s>>>(M, csr, r0, U, A0c, a);
         VEST_LAUNCH("core_g_pass_kernel");
-        core_vec_merge_kernel<<<(unsigned)ceil_div(blk.b, 32), 256, 0, s>>>(bf.part, nctas_g, blk.b, gvec);
-        VEST_LAUNCH("core_vec_merge_kernel");
+        VEST_TRY(vec_merge(bf.part, nctas_g, blk.b, gvec, bf.part + (size_t)kCorePassCtas * kCoreMaxB, s));
       } else {
         VEST_CUDA(cudaMemsetAsync(gvec, 0, (size_t)blk.b * 8, s));
       }
@@ -1046,7 +1145,19 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
       a.prev = blk;
     }
   }
-  return VEST_OK;
+  if (!final_loss) return VEST_OK;
+  // the last block's change still has to reach r; then the loss sums and the COO copy
+  const int nl = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->nnz, 1024), loss_ctas()));
+  double* lpart = reinterpret_cast<double*>(scratch + plan.off_part);
+  if (ix->nnz > 0) {
+    core_u_kernel<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->mode[0].cap, 256), num_sms() * 4)),
+                       256, 0, s>>>(M, csr.nzrow, csr.nnzrows, dbuf[(iblk + 1) & 1], c.J0, a.prev.m, U);
+    VEST_LAUNCH("core_u_kernel");
+    core_final_kernel<T><<<nl, 256, 0, s>>>(M, csr, r0, reinterpret_cast<T*>(scratch + plan.off_resid_coo), U, a.prev,
+                                            lpart);
+    VEST_LAUNCH("core_final_kernel");
+  }
+  return loss_finish<T>(mdl, reg, lambda, ix->nnz > 0 ? nl : 0, final_loss, scratch, plan, s);
 }
 
 template <typename T>
@@ -1090,8 +1201,7 @@ vest_status core_responsibility(const vest_index* ix, const vest_model* mdl, con
         case 16: VEST_TRY(launch_stats<T, 16>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
         default: VEST_TRY(launch_stats<T, 32>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
       }
-      core_vec_merge_kernel<<<(unsigned)ceil_div(nacc, 32), 256, 0, s>>>(bf.part, nctas, nacc, sums);
-      VEST_LAUNCH("core_vec_merge_kernel");
+      VEST_TRY(vec_merge(bf.part, nctas, nacc, sums, bf.part + (size_t)kCorePassCtas * nacc, s));
     } else {
       VEST_CUDA(cudaMemsetAsync(sums, 0, (size_t)nacc * 8, s));
     }
@@ -1103,9 +1213,9 @@ vest_status core_responsibility(const vest_index* ix, const vest_model* mdl, con
 }
 
 template vest_status sweep_core_impl<float>(const vest_index*, const vest_model*, int, double, char*,
-                                            const ScratchPlan&, cudaStream_t);
+                                            const ScratchPlan&, cudaStream_t, double*);
 template vest_status sweep_core_impl<double>(const vest_index*, const vest_model*, int, double, char*,
-                                             const ScratchPlan&, cudaStream_t);
+                                             const ScratchPlan&, cudaStream_t, double*);
 template vest_status core_responsibility<float>(const vest_index*, const vest_model*, const float*, const double*,
                                                 double*, double*, char*, const ScratchPlan&, cudaStream_t);
 template vest_status core_responsibility<double>(const vest_index*, const vest_model*, const double*, const double*,

@@ -383,12 +383,17 @@ __device__ __forceinline__ int load_task_rows(const int64_t* __restrict__ nzptr,
 }
 
 // ---------------------------------------------------------------- per-piece sums
-// sums[k * P + p] = sum over the entries q of row piece k (task-local positions
-// [max(sptr[k], t0), min(sptr[k+1], t1)) - t0) of f.eval(f.prep(p), q).
-// Pieces of at most kPieceChunk entries: one warp per piece, lanes over p.
-// Longer pieces (at most TASK / kPieceChunk of them): cut into kPieceChunk-entry
-// chunks spread over every thread, partials combined in chunk order.  Each
-// chain keeps two accumulators (even / odd entries).  Fixed order throughout.
+// The task's staged vectors V[q][0..L), L even: delta_0 .. delta_{JN-1}, X, 0 for the
+// task-local entries q.  A tile sums four products over the entries of a row piece
+// (task-local positions [max(sptr[k], t0), min(sptr[k+1], t1)) - t0):
+//   outer tile (ca, cb):  A = V[q][ca, ca+1], B = V[q][cb, cb+1]:  A0 B0, A0 B1, A1 B0, A1 B1
+//   square tile (ca):     A = V[q][ca, ca+1], x = V[q][xcol]:      x A0, x A1, A0^2, A1^2
+// into the outputs out.x, .y, .z, .w of the piece (-1: none).  Every output of a piece
+// belongs to exactly one tile.  Pieces of at most kPieceChunk entries: one warp per
+// piece, lanes over tiles.  Longer pieces (at most TASK / kPieceChunk + 1 of them): cut
+// into kPieceChunk-entry chunks spread over every thread, partials combined in chunk
+// order.  Each chain keeps two accumulator sets (even / odd entries).  Fixed order
+// throughout.
 constexpr int kPieceChunk = 32;
 constexpr int kMaxLongPieces = 16;
 
@@ -400,40 +405,76 @@ struct PieceScratch {
   int item0[kMaxLongPieces + 1];   // first item of each long piece
 };
 
-// A term is pa[q * sa] * pb[q * sb] over the piece's task-local entries q.
 template <typename S>
-struct TermPtrs {
-  const S* pa;
-  const S* pb;
-  int sa, sb;
-};
-
-template <typename S, typename F>
-__device__ __forceinline__ S chain_sum(const F& f, const TermPtrs<S>& pr, int s, int e) {
-  (void)f;
-  S a0 = S(0), a1 = S(0);
-  const S* pa = pr.pa + s * pr.sa;
-  const S* pb = pr.pb + s * pr.sb;
-  int q = s;
-  for (; q + 1 < e; q += 2) {
-    a0 += pa[0] * pb[0];
-    a1 += pa[pr.sa] * pb[pr.sb];
-    pa += 2 * pr.sa;
-    pb += 2 * pr.sb;
+__device__ __forceinline__ void load2(const S* p, S& a, S& b) {
+  if constexpr (sizeof(S) == 4) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    a = v.x;
+    b = v.y;
+  } else {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    a = v.x;
+    b = v.y;
   }
-  if (q < e) a0 += pa[0] * pb[0];
-  return a0 + a1;
 }
 
-template <typename S, typename F>
-__device__ void piece_sums(const int64_t* sptr, int nrows, int64_t t0, int64_t t1, int P, S* sums, S* part,
-                           PieceScratch* ps, const F& f) {
+template <typename S, bool SQUARE>
+__device__ __forceinline__ void tile_chain(const S* V, int L, int xcol, int2 cab, int s, int e, S (&r)[4]) {
+  S a[4] = {S(0), S(0), S(0), S(0)}, b[4] = {S(0), S(0), S(0), S(0)};
+  const S* p = V + s * L;
+  int q = s;
+  for (; q + 1 < e; q += 2, p += 2 * L) {
+    S x0, x1, y0, y1;
+    load2<S>(p + cab.x, x0, x1);
+    load2<S>(p + L + cab.x, y0, y1);
+    if constexpr (SQUARE) {
+      const S u = p[xcol], v = p[L + xcol];
+      a[0] += u * x0; a[1] += u * x1; a[2] += x0 * x0; a[3] += x1 * x1;
+      b[0] += v * y0; b[1] += v * y1; b[2] += y0 * y0; b[3] += y1 * y1;
+    } else {
+      S u0, u1, v0, v1;
+      load2<S>(p + cab.y, u0, u1);
+      load2<S>(p + L + cab.y, v0, v1);
+      a[0] += x0 * u0; a[1] += x0 * u1; a[2] += x1 * u0; a[3] += x1 * u1;
+      b[0] += y0 * v0; b[1] += y0 * v1; b[2] += y1 * v0; b[3] += y1 * v1;
+    }
+  }
+  if (q < e) {
+    S x0, x1;
+    load2<S>(p + cab.x, x0, x1);
+    if constexpr (SQUARE) {
+      const S u = p[xcol];
+      a[0] += u * x0; a[1] += u * x1; a[2] += x0 * x0; a[3] += x1 * x1;
+    } else {
+      S u0, u1;
+      load2<S>(p + cab.y, u0, u1);
+      a[0] += x0 * u0; a[1] += x0 * u1; a[2] += x1 * u0; a[3] += x1 * u1;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r[i] = a[i] + b[i];
+}
+
+__device__ __forceinline__ int out_at(const int4& o, int i) { return i == 0 ? o.x : i == 1 ? o.y : i == 2 ? o.z : o.w; }
+
+template <typename S, bool SQUARE>
+__device__ void piece_sums(const int64_t* sptr, int nrows, int64_t t0, int64_t t1, int NT, int P, const int2* cab,
+                           const int4* outs, const S* V, int L, int xcol, S* sums, S* part, PieceScratch* ps) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   // short pieces
   for (int k = warp; k < nrows; k += nwarps) {
     const int s = (int)(max(sptr[k], t0) - t0), e = (int)(min(sptr[k + 1], t1) - t0);
     if (e - s > kPieceChunk) continue;
-    for (int p = lane; p < P; p += 32) sums[k * P + p] = chain_sum<S>(f, f.prep(p), s, e);
+    for (int t = lane; t < NT; t += 32) {
+      S r[4];
+      tile_chain<S, SQUARE>(V, L, xcol, cab[t], s, e, r);
+      const int4 o = outs[t];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int pi = out_at(o, i);
+        if (pi >= 0) sums[k * P + pi] = r[i];
+      }
+    }
   }
   // collect long pieces (warp 0)
   if (warp == 0) {
@@ -458,7 +499,7 @@ __device__ void piece_sums(const int64_t* sptr, int nrows, int64_t t0, int64_t t
         const int len = (int)(min(sptr[k + 1], t1) - max(sptr[k], t0));
         ps->q[i] = (len + kPieceChunk - 1) / kPieceChunk;
         ps->item0[i] = it;
-        it += ps->q[i] * P;
+        it += ps->q[i] * NT;
       }
       ps->item0[ps->nlong] = it;
       ps->total = it;
@@ -470,18 +511,24 @@ __device__ void piece_sums(const int64_t* sptr, int nrows, int64_t t0, int64_t t
     int j = 0;
     while (i >= ps->item0[j + 1]) ++j;
     const int k = ps->k[j], r = i - ps->item0[j];
-    const int q = r / P, p = r % P;
+    const int q = r / NT, t = r % NT;
     const int s0 = (int)(max(sptr[k], t0) - t0), e0 = (int)(min(sptr[k + 1], t1) - t0);
     const int s = s0 + q * kPieceChunk, e = min(e0, s + kPieceChunk);
-    part[i] = chain_sum<S>(f, f.prep(p), s, e);
+    S rr[4];
+    tile_chain<S, SQUARE>(V, L, xcol, cab[t], s, e, rr);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) part[i * 4 + u] = rr[u];
   }
   __syncthreads();
   for (int j = 0; j < nlong; ++j) {
     const int k = ps->k[j], nq = ps->q[j], base = ps->item0[j];
-    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    for (int tu = threadIdx.x; tu < NT * 4; tu += blockDim.x) {
+      const int t = tu >> 2, u = tu & 3;
+      const int pi = out_at(outs[t], u);
+      if (pi < 0) continue;
       S a = S(0);
-      for (int q = 0; q < nq; ++q) a += part[base + q * P + p];
-      sums[k * P + p] = a;
+      for (int q = 0; q < nq; ++q) a += part[(base + q * NT + t) * 4 + u];
+      sums[k * P + pi] = a;
     }
   }
   __syncthreads();

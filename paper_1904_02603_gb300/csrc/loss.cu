@@ -54,24 +54,25 @@ __global__ void __launch_bounds__(kLossTask / E, (delta_min_blocks<T, JN, JF, E>
   const ModeRoles& r = a.r;
   const int64_t core_elems = r.n_outer * r.Jf * JN;
   T* sG = reinterpret_cast<T*>(smem_raw);
-  size_t off = a.use_smem_core ? (size_t)core_elems * sizeof(T) : 0;
-  off = (off + 15) & ~(size_t)15;
-  int64_t* sptr = reinterpret_cast<int64_t*>(smem_raw + off);
   const T* g = gcore;
   if (a.use_smem_core) {
     for (int64_t e = threadIdx.x; e < core_elems; e += blockDim.x) sG[e] = gcore[e];
     g = sG;
   }
-  const int R = *csr.nnzrows;
   const int64_t nnz = csr.nnz;
   const int J0 = M.J[0];
-  double sq = 0.0, xx = 0.0;
+  // per-thread sums in the storage type with Kahan compensation, FP64 across threads
+  T sq = T(0), sqc = T(0), xx = T(0), xxc = T(0);
+  auto kadd = [](T& s, T& c, T v) {
+    const T y = v - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  };
   __syncthreads();
   for (int64_t task = blockIdx.x; task < a.ntasks; task += gridDim.x) {
     const int64_t t0 = task * kLossTask, t1 = min(t0 + (int64_t)kLossTask, nnz);
     const int cnt = (int)(t1 - t0);
-    int64_t k0;
-    const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, sptr, &k0);
     if ((int)threadIdx.x < cnt) {
       const T* rowf[E];
       SlowRows sr[E];
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(kLossTask / E, (delta_min_blocks<T, JN, JF, E>
         const int q = threadIdx.x + e * blockDim.x;
         if (q >= cnt) continue;
         const int64_t p = t0 + q;
-        const int64_t i0 = csr.nzrow[k0 + local_row(sptr, nrows, p)];
+        const int64_t i0 = csr.nzrow[csr.rowk[p]];
         const T* a0 = M.A[0] + i0 * J0;
         T b = T(0);
 #pragma unroll
@@ -97,14 +98,13 @@ __global__ void __launch_bounds__(kLossTask / E, (delta_min_blocks<T, JN, JF, E>
         const T res = x - b;
         if (resid_csr0) resid_csr0[p] = res;
         if (resid_coo) resid_coo[csr.perm[p]] = res;
-        sq += (double)res * (double)res;
-        xx += (double)x * (double)x;
+        kadd(sq, sqc, res * res);
+        kadd(xx, xxc, x * x);
       }
     }
-    __syncthreads();
   }
-  const double s1 = block_sum(sq, red);
-  const double s2 = block_sum(xx, red);
+  const double s1 = block_sum((double)sq - (double)sqc, red);
+  const double s2 = block_sum((double)xx - (double)xxc, red);
   if (threadIdx.x == 0) {
     a.part[blockIdx.x * 2 + 0] = s1;
     a.part[blockIdx.x * 2 + 1] = s2;
@@ -195,8 +195,8 @@ vest_status loss_impl(const vest_index* ix, const vest_model* m, int reg, double
   a.onz = onz;
   a.ntasks = ceil_div(ix->nnz, kLossTask);
   const size_t core_bytes = align_up((size_t)core_elems * sizeof(T), 16);
-  a.use_smem_core = core_bytes + (kLossTask + 2) * 8 <= kLossSmemBudget;
-  const size_t smem = (a.use_smem_core ? core_bytes : 0) + (kLossTask + 2) * 8;
+  a.use_smem_core = core_bytes <= kLossSmemBudget;
+  const size_t smem = a.use_smem_core ? core_bytes : 0;
   double* lpart = reinterpret_cast<double*>(scratch + plan.off_part);
   double* rpart = lpart + 2 * kLossCtas;
   a.part = lpart;
@@ -220,6 +220,28 @@ vest_status loss_impl(const vest_index* ix, const vest_model* m, int reg, double
 }
 
 size_t loss_part_bytes() { return (size_t)(2 * kLossCtas + kRegCtas) * 8; }
+
+// Loss from per-CTA (sum r^2, sum x^2) partials already in the loss region (nl of them,
+// at most kLossCtas): adds the regulariser and writes the five loss values.
+template <typename T>
+vest_status loss_finish(const vest_model* m, int reg, double lambda, int nl, double* out, char* scratch,
+                        const ScratchPlan& plan, cudaStream_t s) {
+  const DevModel<T> M = dev_model<T>(m);
+  double* lpart = reinterpret_cast<double*>(scratch + plan.off_part);
+  double* rpart = lpart + 2 * kLossCtas;
+  reg_kernel<T><<<kRegCtas, 256, 0, s>>>(M, reg, rpart);
+  VEST_LAUNCH("reg_kernel");
+  loss_final_kernel<<<1, 256, 0, s>>>(lpart, nl, rpart, kRegCtas, lambda, out);
+  VEST_LAUNCH("loss_final_kernel");
+  return VEST_OK;
+}
+
+int loss_ctas() { return kLossCtas; }
+
+template vest_status loss_finish<float>(const vest_model*, int, double, int, double*, char*, const ScratchPlan&,
+                                        cudaStream_t);
+template vest_status loss_finish<double>(const vest_model*, int, double, int, double*, char*, const ScratchPlan&,
+                                         cudaStream_t);
 
 template vest_status loss_impl<float>(const vest_index*, const vest_model*, int, double, double*, float*, float*, char*,
                                       const ScratchPlan&, cudaStream_t);

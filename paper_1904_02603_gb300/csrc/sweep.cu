@@ -97,20 +97,52 @@ __device__ void finish_row(const DevModel<T>& M, int n, int64_t row, const S* su
   }
 }
 
-// Terms of the row sums from a per-block table: output p < Jn is X (or r) times
-// delta_j; the rest are delta_j delta_t (packed upper Gram) or delta_j^2.
-template <typename T>
-struct SweepTerm {
-  const T* sD;
-  const T* sX;
-  const int2* tab;  // (j, t); t < 0: X delta_j
-  int JNS;
-  __device__ TermPtrs<T> prep(int p) const {
-    const int2 jt = tab[p];
-    if (jt.y < 0) return TermPtrs<T>{sX, sD + jt.x, 1, JNS};
-    return TermPtrs<T>{sD + jt.x, sD + jt.y, JNS, JNS};
+// Chunks of the long pieces of one task: sum of ceil(len / kPieceChunk) over pieces
+// longer than kPieceChunk, at most task / kPieceChunk + task / (kPieceChunk + 1).
+__host__ __device__ inline int long_chunks(int task) { return task / kPieceChunk + task / (kPieceChunk + 1); }
+
+// Row-sum tiles over the staged vectors V = (delta_0 .. delta_{JN-1}, X, 0).
+// kModeUpdate: outer 2 x 2 tiles (I, J), I <= J over column pairs, the (X, 0) pair
+// with itself left out; each product delta_j delta_t (j <= t < Jn) goes to the packed
+// Gram output Jn + packed(j, t), X delta_j to output j.  kModeResp: square tiles, one
+// per pair of columns: r delta_j to output j, delta_j^2 to output Jn + j.
+__host__ __device__ inline int sweep_tiles(int JN, int mode) {
+  const int nb = (JN + 2) / 2;
+  return mode == kModeUpdate ? nb * (nb + 1) / 2 - 1 : JN / 2;
+}
+
+__device__ inline void sweep_tile(int t, int JN, int Jn, int mode, int2& cab, int4& out) {
+  int o[4] = {-1, -1, -1, -1};
+  if (mode == kModeUpdate) {
+    const int nb = (JN + 2) / 2;
+    int I = 0, u = t;
+    while (u >= nb - I) {
+      u -= nb - I;
+      ++I;
+    }
+    const int J = I + u;
+    cab = make_int2(2 * I, 2 * J);
+    for (int i = 0; i < 4; ++i) {
+      const int j = 2 * I + (i >> 1), tt = 2 * J + (i & 1);
+      if (I == J && (i >> 1) > (i & 1)) continue;  // the lower copy of a diagonal tile
+      if (j >= Jn) continue;
+      if (tt < Jn) o[i] = Jn + packed_row(j, Jn) + (tt - j);
+      else if (tt == JN) o[i] = j;
+    }
+  } else {
+    cab = make_int2(2 * t, 0);
+    const int j0 = 2 * t, j1 = 2 * t + 1;
+    if (j0 < Jn) {
+      o[0] = j0;
+      o[2] = Jn + j0;
+    }
+    if (j1 < Jn) {
+      o[1] = j1;
+      o[3] = Jn + j1;
+    }
   }
-};
+  out = make_int4(o[0], o[1], o[2], o[3]);
+}
 
 template <typename T, int JN, int JF, int NSLOW, int MODE, int E>
 __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 / E))) sweep_task_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ gcore,
@@ -118,26 +150,29 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ModeRoles& r = a.r;
   const int TASK = a.task, KMAX = a.kmax;
-  const int JNS = JN + 1;
+  constexpr int L = JN + 2;  // staged vector: delta_0 .. delta_{JN-1}, X, 0
   const int P = a.P;
+  const int NT = sweep_tiles(JN, MODE);
   const int64_t core_elems = r.n_outer * r.Jf * JN;
-  // shared layout: core | sptr | D | X | acc | long-piece partials | term table
+  // shared layout: core | sptr | V | acc | long-piece partials | tile table
   T* sG = reinterpret_cast<T*>(smem_raw);
   size_t off = a.use_smem_core ? (size_t)core_elems * sizeof(T) : 0;
   off = (off + 15) & ~(size_t)15;
   int64_t* sptr = reinterpret_cast<int64_t*>(smem_raw + off);
   off += (size_t)(TASK + 2) * 8;
-  T* sD = reinterpret_cast<T*>(smem_raw + off);
-  off += (size_t)TASK * JNS * sizeof(T);
-  T* sX = reinterpret_cast<T*>(smem_raw + off);
-  off += (size_t)TASK * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  T* sV = reinterpret_cast<T*>(smem_raw + off);
+  off += (size_t)TASK * L * sizeof(T);
   off = (off + 15) & ~(size_t)15;
   T* sAcc = reinterpret_cast<T*>(smem_raw + off);
   off += (size_t)KMAX * P * sizeof(T);
   T* sPart = reinterpret_cast<T*>(smem_raw + off);
-  off += (size_t)kMaxLongPieces * P * sizeof(T);
-  int2* sTab = reinterpret_cast<int2*>(smem_raw + off);
-  off += (size_t)P * sizeof(int2);
+  off += (size_t)long_chunks(TASK) * NT * 4 * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  int4* sOut = reinterpret_cast<int4*>(smem_raw + off);
+  off += (size_t)NT * sizeof(int4);
+  int2* sCab = reinterpret_cast<int2*>(smem_raw + off);
+  off += (size_t)NT * sizeof(int2);
   off = (off + 15) & ~(size_t)15;
   T* sCarry = reinterpret_cast<T*>(smem_raw + off);  // [2][sum, compensation][P]: row sums carried to the next task
   __shared__ PieceScratch pscr;
@@ -147,21 +182,7 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
     for (int64_t e = threadIdx.x; e < core_elems; e += blockDim.x) sG[e] = gcore[e];
     g = sG;
   }
-  const int Jn = r.Jn;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
-    if (p < Jn) {
-      sTab[p] = make_int2(p, -1);
-    } else if constexpr (MODE == kModeUpdate) {
-      int u = p - Jn, j = 0;
-      while (u >= Jn - j) {
-        u -= Jn - j;
-        ++j;
-      }
-      sTab[p] = make_int2(j, j + u);
-    } else {
-      sTab[p] = make_int2(p - Jn, p - Jn);
-    }
-  }
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) sweep_tile(t, JN, r.Jn, MODE, sCab[t], sOut[t]);
   const int R = *csr.nnzrows;
   const int64_t nnz = csr.nnz;
   __syncthreads();
@@ -193,21 +214,21 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
       for (int e = 0; e < E; ++e) {
         const int q = threadIdx.x + e * blockDim.x;
         if (q < cnt) {
-          T* dst = sD + q * JNS;
+          T* dst = sV + q * L;
 #pragma unroll
           for (int j = 0; j < JN; ++j) dst[j] = d[e][j];
-          if constexpr (MODE == kModeUpdate) sX[q] = csr.val[t0 + q];
-          else sX[q] = static_cast<const T*>(a.resid_coo)[csr.perm[t0 + q]];
+          if constexpr (MODE == kModeUpdate) dst[JN] = csr.val[t0 + q];
+          else dst[JN] = static_cast<const T*>(a.resid_coo)[csr.perm[t0 + q]];
+          dst[JN + 1] = T(0);
         }
       }
     }
     __syncthreads();
 
-    const SweepTerm<T> f{sD, sX, sTab, JNS};
     for (int r0 = 0; r0 < nrows; r0 += KMAX) {
       const int nr = min(KMAX, nrows - r0);
       // phase 2: per-row sums over the task's pieces r0 .. r0 + nr - 1
-      piece_sums<T>(sptr + r0, nr, t0, t1, P, sAcc, sPart, &pscr, f);
+      piece_sums<T, MODE == kModeResp>(sptr + r0, nr, t0, t1, NT, P, sCab, sOut, sV, L, JN, sAcc, sPart, &pscr);
       // phase 3: store the sums of rows that end here; carry a row that continues into
       // the block's next task; spill rows cut by the edges of the block's task range
       for (int kr = threadIdx.x; kr < nr; kr += blockDim.x) {
@@ -329,6 +350,7 @@ static int outputs_per_row(int Jn, int mode_kind) {
 }
 
 constexpr size_t kSmemBudget = 200 * 1024;
+constexpr size_t kSmemMax = 227 * 1024;
 constexpr size_t kAccBudget = 32 * 1024;
 constexpr int kTask = 256;
 constexpr int64_t kSweepBlocks = 2432;
@@ -339,15 +361,17 @@ static int pieces_per_round(int P) {
 }
 
 template <typename T>
-static size_t task_smem(int task, int kmax, int JN, int P, size_t core_bytes) {
+static size_t task_smem(int task, int kmax, int JN, int P, int mode, size_t core_bytes) {
+  const int NT = sweep_tiles(JN, mode);
   size_t off = (core_bytes + 15) & ~(size_t)15;
   off += (size_t)(task + 2) * 8;
-  off += (size_t)task * (JN + 1) * sizeof(T);
-  off += (size_t)task * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  off += (size_t)task * (JN + 2) * sizeof(T);
   off = (off + 15) & ~(size_t)15;
   off += (size_t)kmax * P * sizeof(T);
-  off += (size_t)kMaxLongPieces * P * sizeof(T);
-  off += (size_t)P * sizeof(int2);
+  off += (size_t)long_chunks(task) * NT * 4 * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  off += (size_t)NT * (sizeof(int4) + sizeof(int2));
   off = (off + 15) & ~(size_t)15;
   off += 4 * (size_t)P * sizeof(T);
   return off;
@@ -357,7 +381,9 @@ static size_t task_smem(int task, int kmax, int JN, int P, size_t core_bytes) {
 template <typename T>
 int sweep_task_size(int Jn, int P, int64_t core_elems, int* use_smem_core) {
   const int JN = jn_bucket(Jn);
-  *use_smem_core = task_smem<T>(kTask, pieces_per_round<T>(P), JN, P, (size_t)core_elems * sizeof(T)) <= kSmemBudget;
+  // the update's tiles outnumber the responsibility's: size for the update
+  *use_smem_core =
+      task_smem<T>(kTask, pieces_per_round<T>(P), JN, P, kModeUpdate, (size_t)core_elems * sizeof(T)) <= kSmemBudget;
   return kTask;
 }
 
@@ -440,7 +466,12 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
   empty_rows_kernel<T, MODE><<<eg, 256, 0, s>>>(M, n, ix->mode[n].row_ptr, a.delta, a.resp);
   VEST_LAUNCH("empty_rows_kernel");
   if (ix->nnz == 0) return VEST_OK;
-  const size_t smem = task_smem<T>(a.task, a.kmax, JN, a.P, use_smem ? (size_t)core_elems * sizeof(T) : 0);
+  size_t smem = task_smem<T>(a.task, a.kmax, JN, a.P, MODE, use_smem ? (size_t)core_elems * sizeof(T) : 0);
+  while (smem > kSmemMax && a.kmax > 1) {  // large ranks in FP64: fewer pieces per round
+    a.kmax = std::max(1, a.kmax / 2);
+    smem = task_smem<T>(a.task, a.kmax, JN, a.P, MODE, use_smem ? (size_t)core_elems * sizeof(T) : 0);
+  }
+  if (smem > kSmemMax) return fail(VEST_ERR_UNSUPPORTED, "factor sweep: shared memory of one task exceeds 227 KB");
   VEST_TRY(dispatch_jn<T, MODE>(JN, r.nslow, r.Jf, M, csr, gp, a, smem, s));
   const size_t fsmem = (size_t)std::max(1, 256 / a.P) * a.P * 8 + 8 * a.P;
   auto fk = sweep_fixup_kernel<T, MODE>;

@@ -174,9 +174,16 @@ vest_status responsibility_factors(const vest_index* ix, const vest_model* m, co
 template <typename T>
 vest_status loss_impl(const vest_index* ix, const vest_model* m, int reg, double lambda, double* out,
                       T* resid_csr0, T* resid_coo, char* scratch, const ScratchPlan& plan, cudaStream_t s);
+// With final_loss set, the core sweep also applies the last block's change to the residual,
+// stores the residual in COO order and writes the five loss values of the swept model
+// there (device, FP64): the residual then serves the responsibility without a new pass.
 template <typename T>
 vest_status sweep_core_impl(const vest_index* ix, const vest_model* m, int reg, double lambda, char* scratch,
-                            const ScratchPlan& plan, cudaStream_t s);
+                            const ScratchPlan& plan, cudaStream_t s, double* final_loss = nullptr);
+template <typename T>
+vest_status loss_finish(const vest_model* m, int reg, double lambda, int nl, double* out, char* scratch,
+                        const ScratchPlan& plan, cudaStream_t s);
+int loss_ctas();
 template <typename T>
 vest_status core_responsibility(const vest_index* ix, const vest_model* m, const T* resid_csr0,
                                 const double* stats, double* delta_core, double* resp_core, char* scratch,

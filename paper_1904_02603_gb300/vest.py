@@ -76,6 +76,8 @@ _SIGS = {
     "vest_sweep_core": (C.c_int, [_P, C.POINTER(vest_model), C.c_int32, C.c_double, _P, C.c_size_t, _P]),
     "vest_loss": (C.c_int, [_P, C.POINTER(vest_model), C.c_int32, C.c_double, _P, _P, _P, C.c_size_t, _P]),
     "vest_responsibility": (C.c_int, [_P, C.POINTER(vest_model), _P, _P, _P, _P, _P, C.c_size_t, _P]),
+    "vest_iteration": (C.c_int, [_P, C.POINTER(vest_model), C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                 _P, _P, _P, _P, _P, C.c_size_t, _P]),
     "vest_prune": (C.c_int, [C.POINTER(vest_model), _P, _P, C.c_double, C.c_int32, C.c_int32, C.c_double, _P, _P,
                              C.c_size_t, _P]),
     "vest_normalize": (C.c_int, [C.POINTER(vest_model), _P, C.c_size_t, _P]),
@@ -355,6 +357,26 @@ def vest_prune(m: Model, delta_factor, delta_core, pr: float, scratch: torch.Ten
     _call("vest_prune", C.byref(m.cstruct()), C.cast(dfa, C.c_void_p), _dptr(delta_core.contiguous()), pr,
           count_mode, threshold_mode, tau, _dptr(n_pruned), _dptr(scratch), scratch.numel(), _stream(stream))
     return n_pruned
+
+
+def vest_iteration(ix: Index, m: Model, reg: int, lam: float, pr: float, scratch: torch.Tensor, count_mode: int = 0,
+                   with_responsibility: bool = True, factor_sweep: bool = True, stream=None):
+    """One iteration of Algorithm 2 in one call.
+
+    Returns (loss, delta_factor list or None, delta_core or None, n_pruned or None): loss is the
+    device double[5] of vest_loss for the swept model (before the prune)."""
+    loss = torch.empty(5, dtype=torch.float64, device="cuda")
+    df = dc = n_pruned = None
+    dfa = None
+    if with_responsibility:
+        df = [torch.empty(f.shape, dtype=torch.float64, device="cuda") for f in m.factors]
+        dc = torch.empty(m.core.shape, dtype=torch.float64, device="cuda")
+        n_pruned = torch.zeros(m.order + 1, dtype=torch.int64, device="cuda")
+        dfa = _ptr_array(df)
+    _call("vest_iteration", ix.handle, C.byref(m.cstruct()), reg, lam, pr, count_mode, int(factor_sweep),
+          _dptr(loss), C.cast(dfa, C.c_void_p) if dfa is not None else None, _dptr(dc), _dptr(n_pruned),
+          _dptr(scratch), scratch.numel(), _stream(stream))
+    return loss, df, dc, n_pruned
 
 
 def vest_normalize(m: Model, scratch: torch.Tensor, stream=None):

@@ -224,6 +224,70 @@ def test_fp32_objective_within_1e4_on_zipf_workload():
     assert max(errs) < 1e-4
 
 
+# ---------------------------------------------------------------- one iteration in one call (Algorithm 2)
+@pytest.mark.parametrize("reg", [0, 1])
+@pytest.mark.parametrize("name", list(CASES))
+def test_iteration_f64(name, reg):
+    """vest_iteration against the oracle's sweeps, loss, responsibility and prune in turn."""
+    if reg == 1 and name not in ("n3_ragged", "zipf_heavy", "n5_generic"):
+        pytest.skip("L1 on a subset")
+    t, st = make_case(name)
+    st = with_masks(st, 0.05, 13)
+    ten, mdl = device_pair(t, st)
+    ix = V.vest_build_index(ten)
+    sc = V.make_scratch(ix, mdl)
+    prob, om = oracle_pair(t, st)
+    lam = 0.05
+    for it in range(2):
+        loss, df, dc, npr = V.vest_iteration(ix, mdl, reg, lam, 0.05, sc)
+        O.sweep_factors(prob, om, reg, lam, -1)
+        O.sweep_core(prob, om, reg, lam)
+        oloss = O.loss(prob, om, reg, lam)
+        odf, odc, _, _ = O.responsibility(prob, om)
+        onp = O.prune(om, odf, odc, 0.05, 0)
+        assert rel_err(loss.cpu().numpy(), oloss) < TOL64, (it, loss.cpu().numpy(), oloss)
+        for n in range(t.N):
+            assert rel_err(df[n].cpu().numpy(), odf[n]) < TOL64
+        assert rel_err(dc.cpu().numpy(), odc) < TOL64
+        np.testing.assert_array_equal(npr.cpu().numpy(), onp)
+        assert masks_equal(mdl, om)
+        assert model_err(mdl, om) < TOL64
+
+
+def test_iteration_without_responsibility_matches_separate_calls():
+    t, st = make_case("zipf_heavy")
+    ten, m1 = device_pair(t, st)
+    _, m2 = device_pair(t, st)
+    ix = V.vest_build_index(ten)
+    sc = V.make_scratch(ix, m1)
+    loss, df, dc, npr = V.vest_iteration(ix, m1, V.REG_LF, 0.01, 0.0, sc, with_responsibility=False)
+    assert df is None and dc is None and npr is None
+    V.vest_sweep_factors(ix, m2, V.REG_LF, 0.01, -1, sc)
+    V.vest_sweep_core(ix, m2, V.REG_LF, 0.01, sc)
+    ref = V.vest_loss(ix, m2, V.REG_LF, 0.01, sc)
+    assert rel_err(loss.cpu().numpy(), ref.cpu().numpy()) < 1e-12
+    f1, c1, _, _ = m1.to_host()
+    f2, c2, _, _ = m2.to_host()
+    assert all(np.array_equal(a, b) for a, b in zip(f1, f2)) and np.array_equal(c1, c2)
+
+
+def test_iteration_fp32_objective_within_1e4_on_zipf_workload():
+    """The residual kept by the core sweep (FP32, updated block by block) gives the loss within 1e-4."""
+    t, st, _ = datagen.make("c1_small")
+    ten, mdl = device_pair(t, st, torch.float32)
+    ix = V.vest_build_index(ten)
+    sc = V.make_scratch(ix, mdl)
+    prob, om = oracle_pair(t, st)
+    for it in range(3):
+        loss, _, _, _ = V.vest_iteration(ix, mdl, V.REG_LF, 0.01, 0.0, sc)
+        O.sweep_factors(prob, om, O.REG_LF, 0.01, -1)
+        O.sweep_core(prob, om, O.REG_LF, 0.01)
+        ref = O.loss(prob, om, O.REG_LF, 0.01)
+        got = loss.cpu().numpy()
+        assert abs(got[3] - ref[3]) / ref[3] < 1e-4, (it, got, ref)
+        assert abs(got[4] - ref[4]) / ref[4] < 1e-4
+
+
 # ---------------------------------------------------------------- edge cases
 def test_empty_tensor_zeroes_everything():
     dims, ranks = (5, 4, 3), (2, 2, 2)
