@@ -304,13 +304,13 @@ vest_status vest_iteration(const vest_index* ix, vest_model* m, int32_t reg, dou
     if (!resp) return VEST_OK;
     const double* r0 = reinterpret_cast<const double*>(sc + plan.off_resid);
     VEST_TRY(responsibility_factors<double>(ix, m, loss, delta_factor, nullptr, sc, plan, s));
-    VEST_TRY(core_responsibility<double>(ix, m, r0, loss, delta_core, nullptr, sc, plan, s));
+    VEST_TRY(core_responsibility<double>(ix, m, r0, loss, delta_core, nullptr, sc, plan, s, true));
   } else {
     VEST_TRY(sweep_core_impl<float>(ix, m, reg, lambda, sc, plan, s, loss));
     if (!resp) return VEST_OK;
     const float* r0 = reinterpret_cast<const float*>(sc + plan.off_resid);
     VEST_TRY(responsibility_factors<float>(ix, m, loss, delta_factor, nullptr, sc, plan, s));
-    VEST_TRY(core_responsibility<float>(ix, m, r0, loss, delta_core, nullptr, sc, plan, s));
+    VEST_TRY(core_responsibility<float>(ix, m, r0, loss, delta_core, nullptr, sc, plan, s, true));
   }
   if (m->dtype == VEST_F64)
     return prune_impl<double>(m, delta_factor, delta_core, pr, count_mode, 0, 0.0, n_pruned, sc, plan, s);

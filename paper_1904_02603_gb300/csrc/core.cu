@@ -391,7 +391,7 @@ __global__ void core_a0c_kernel(DevModel<T> M, const int32_t* __restrict__ nzrow
 // suffix weights, u, and the head lanes' a0 rows from A0c) are issued together
 // after the coalesced index loads.
 template <typename T>
-__global__ void __launch_bounds__(256, 3) core_g_pass_kernel(DevModel<T> M, DevMode<T> csr, T* r, const T* __restrict__ U,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) core_g_pass_kernel(DevModel<T> M, DevMode<T> csr, T* r, const T* __restrict__ U,
                                                           const T* __restrict__ A0c, GPassArgs a) {
   constexpr int kPer = kCoreMaxB / 32;
   __shared__ T sh[8][kCoreMaxM];
@@ -406,28 +406,60 @@ __global__ void __launch_bounds__(256, 3) core_g_pass_kernel(DevModel<T> M, DevM
   for (int i = 0; i < kPer; ++i) as[i] = ac[i] = T(0);
   const int64_t nchunks = ceil_div(a.nnz, 32);
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp, nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  // the coalesced loads of a chunk (row, mode-1 index, mode-2 index when N = 3, r) are
-  // issued one chunk ahead
+  // Software pipeline over the warp's chunks: while chunk ch is processed, the gathers of
+  // chunk ch + nw (a1 row, u row, suffix weights) and the coalesced loads of chunk ch + 2 nw
+  // (row, mode-1 index, mode-2 index when N = 3, r) are in flight.
   const bool n3 = M.N == 3;
-  int nk = 0, ni1 = 0, ni2 = 0;
-  T nrv = T(0);
-  auto prefetch = [&](int64_t ch) {
+  struct Idx {
+    int k, i1, i2;
+    T rv;
+  };
+  struct Val {
+    T v[kCoreMaxM], u[kCoreMaxM];
+    T c, cp;
+  };
+  auto load_idx = [&](int64_t ch, Idx& x) {
     const int64_t p = ch * 32 + lane;
     if (ch < nchunks && p < a.nnz) {
-      nk = csr.rowk[p];
-      ni1 = csr.oidx[p];
-      if (n3) ni2 = csr.oidx[a.nnz + p];
-      nrv = r[p];
+      x.k = csr.rowk[p];
+      x.i1 = csr.oidx[p];
+      if (n3) x.i2 = csr.oidx[a.nnz + p];
+      x.rv = r[p];
     }
   };
-  prefetch(gw);
+  auto load_val = [&](int64_t ch, const Idx& x, Val& g) {
+    const int64_t p = ch * 32 + lane;
+    if (ch < nchunks && p < a.nnz) {
+      const T* a1 = M.A[1] + (int64_t)x.i1 * a.J1 + a.cur.q0;
+#pragma unroll
+      for (int q = 0; q < kCoreMaxM; ++q)
+        if (q < m) g.v[q] = a1[q];
+      if (a.has_prev) {
+        const T* u = U + (int64_t)x.k * kCoreMaxM;
+#pragma unroll
+        for (int q = 0; q < kCoreMaxM; ++q)
+          if (q < mp) g.u[q] = u[q];
+        if (n3) g.cp = M.A[2][(int64_t)x.i2 * M.J[2] + a.prev.s];
+        else suffix_weights<T>(M, csr.oidx, a.nnz, p, a.prev.s, 1, &g.cp, 1);
+      }
+      if (n3) g.c = M.A[2][(int64_t)x.i2 * M.J[2] + a.cur.s];
+      else suffix_weights<T>(M, csr.oidx, a.nnz, p, a.cur.s, 1, &g.c, 1);
+    }
+  };
+  Idx xn{0, 0, 0, T(0)}, xnn{0, 0, 0, T(0)};
+  Val gn;
+  load_idx(gw, xn);
+  load_val(gw, xn, gn);
+  load_idx(gw + nw, xnn);
   for (int64_t ch = gw; ch < nchunks; ch += nw) {
     const int64_t p = ch * 32 + lane;
     const bool valid = p < a.nnz;
-    const int k = valid ? nk : -1 - lane;
-    const int i1 = ni1, i2 = ni2;
-    const T rv0 = nrv;
-    prefetch(ch + nw);
+    const Idx xc = xn;
+    const Val gc = gn;
+    xn = xnn;
+    load_val(ch + nw, xn, gn);
+    load_idx(ch + 2 * nw, xnn);
+    const int k = valid ? xc.k : -1 - lane;
     const int kup = __shfl_up_sync(0xffffffffu, k, 1);
     const bool head = valid && (lane == 0 || kup != k);
     T h[kCoreMaxM];
@@ -439,31 +471,20 @@ __global__ void __launch_bounds__(256, 3) core_g_pass_kernel(DevModel<T> M, DevM
       for (int j = 0; j < J0; ++j) sa[lane * J0 + j] = a0[j];
     }
     if (valid) {
-      const T* a1 = M.A[1] + (int64_t)i1 * a.J1;
-      T rv = rv0;
-      T v[kCoreMaxM];
-#pragma unroll
-      for (int q = 0; q < kCoreMaxM; ++q)
-        if (q < m) v[q] = a1[a.cur.q0 + q];
+      T rv = xc.rv;
       if (a.has_prev) {
-        T cp;
-        if (n3) cp = M.A[2][(int64_t)i2 * M.J[2] + a.prev.s];
-        else suffix_weights<T>(M, csr.oidx, a.nnz, p, a.prev.s, 1, &cp, 1);
-        const T* u = U + (int64_t)k * kCoreMaxM;
+        const T* a1p = M.A[1] + (int64_t)xc.i1 * a.J1 + a.prev.q0;
         T acc = T(0);
 #pragma unroll
         for (int q = 0; q < kCoreMaxM; ++q)
-          if (q < mp) acc += (same_q ? v[q] : a1[a.prev.q0 + q]) * u[q];
-        rv -= cp * acc;
+          if (q < mp) acc += (same_q ? gc.v[q] : a1p[q]) * gc.u[q];
+        rv -= gc.cp * acc;
         r[p] = rv;
       }
-      T c;
-      if (n3) c = M.A[2][(int64_t)i2 * M.J[2] + a.cur.s];
-      else suffix_weights<T>(M, csr.oidx, a.nnz, p, a.cur.s, 1, &c, 1);
-      const T rc = rv * c;
+      const T rc = rv * gc.c;
 #pragma unroll
       for (int q = 0; q < kCoreMaxM; ++q)
-        if (q < m) h[q] = rc * v[q];
+        if (q < m) h[q] = rc * gc.v[q];
     }
     // segmented suffix sums: lane l ends with the sum over its row from l to the chunk end
 #pragma unroll
@@ -699,16 +720,20 @@ struct StatsArgs {
   double* part;    // [ctas][2 * J0 * SJ]
 };
 
-// Streams (pairs (j_1, s) of the group) per lane in the stats pass.
-__host__ __device__ constexpr int stats_spl(int J0B) { return J0B <= 12 ? 2 : 1; }
+// Streams (pairs (j_1, s) of the group) per lane in the stats pass: the accumulators
+// (kinds x J0B x streams) stay in registers with two CTAs per SM.
+__host__ __device__ constexpr int stats_spl(int J0B, bool diag) {
+  return diag ? (J0B <= 12 ? 2 : 1) : (J0B <= 12 ? 4 : (J0B <= 16 ? 2 : 1));
+}
 
 // Shared memory of the stats pass: per warp the staged entries and the running sums.
 __host__ __device__ inline size_t stats_stage_elems(int J0, int J1, int Sg) { return (size_t)32 * (J0 + J1 + Sg + 1); }
-__host__ __device__ inline size_t stats_run_elems(int J0, int spl) { return (size_t)2 * 2 * J0 * 32 * spl; }
+__host__ __device__ inline size_t stats_run_elems(int J0, int spl, int kinds) { return (size_t)kinds * 2 * J0 * 32 * spl; }
 
 // Stats pass for one group of Sg suffixes: for every core element (j0, j1, s) of the group
 //   g(j0, j1, s)    = sum_alpha r a0[j0] a1[j1] c(s)
-//   diag(j0, j1, s) = sum_alpha (a0[j0] a1[j1] c(s))^2.
+//   diag(j0, j1, s) = sum_alpha (a0[j0] a1[j1] c(s))^2   (DIAG only: right after a core
+//                     sweep the block Grams hold it already).
 // Each warp takes whole 256-entry tasks of the mode-0 CSR (warp-strided over the grid) and
 // walks them 32 entries at a time: the lanes stage one entry each (row, r, a0 row, a1 row,
 // c(s) of the group) in shared memory; then every lane runs through the 32 entries in order
@@ -717,16 +742,17 @@ __host__ __device__ inline size_t stats_run_elems(int J0, int spl) { return (siz
 // a0 (x) h1 and a0^2 (x) h2 into its task sums; at the end of the task those go into the
 // warp's running sums in shared memory (Kahan).  Warps are combined in warp order in FP64,
 // one partial per CTA.
-template <typename T, int J0B>
+template <typename T, int J0B, bool DIAG>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
     core_stats_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ r, const T* __restrict__ A0c, StatsArgs a) {
-  constexpr int SPL = stats_spl(J0B);
+  constexpr int SPL = stats_spl(J0B, DIAG);
+  constexpr int KINDS = DIAG ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int J0 = a.J0, J1 = a.J1, Sg = a.Sg, SJ = a.SJ;
   const int ld = J0 + J1 + Sg + 1;  // staged entry: a0 row (where a row starts), a1 row, c(s), r
   T* base = reinterpret_cast<T*>(smem_raw);
-  const size_t stage = stats_stage_elems(J0, J1, Sg), run = stats_run_elems(J0, SPL);
+  const size_t stage = stats_stage_elems(J0, J1, Sg), run = stats_run_elems(J0, SPL, KINDS);
   T* st = base + (size_t)warp * stage;
   // running sums of this lane: [kind][j0][i] x (sum, comp), lane-interleaved
   T* rs = base + (size_t)nwarps * stage + (size_t)warp * run;
@@ -806,7 +832,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
 #pragma unroll
               for (int i = 0; i < SPL; ++i) {
                 t1s[j][i] += a0r[j] * h1[i];
-                t2s[j][i] += a0r[j] * a0r[j] * h2[i];
+                if constexpr (DIAG) t2s[j][i] += a0r[j] * a0r[j] * h2[i];
               }
           }
           cur = k;
@@ -820,7 +846,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
         for (int i = 0; i < SPL; ++i) {
           const T y = se[J0 + qo[i]] * se[J0 + J1 + so[i]];
           h1[i] += rv * y;
-          h2[i] += y * y;
+          if constexpr (DIAG) h2[i] += y * y;
         }
       }
     }
@@ -830,7 +856,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
 #pragma unroll
         for (int i = 0; i < SPL; ++i) {
           t1s[j][i] += a0r[j] * h1[i];
-          t2s[j][i] += a0r[j] * a0r[j] * h2[i];
+          if constexpr (DIAG) t2s[j][i] += a0r[j] * a0r[j] * h2[i];
         }
     }
 #pragma unroll
@@ -839,16 +865,18 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
 #pragma unroll
         for (int i = 0; i < SPL; ++i) {
           T* x1 = rs + ((size_t)(0 * J0 + j) * SPL + i) * 64 + lane;
-          T* x2 = rs + ((size_t)(1 * J0 + j) * SPL + i) * 64 + lane;
           CoreAcc<T>::add(x1[0], x1[32], t1s[j][i]);
-          CoreAcc<T>::add(x2[0], x2[32], t2s[j][i]);
+          if constexpr (DIAG) {
+            T* x2 = rs + ((size_t)(1 * J0 + j) * SPL + i) * 64 + lane;
+            CoreAcc<T>::add(x2[0], x2[32], t2s[j][i]);
+          }
         }
       }
     }
   }
   // warps in order, FP64: red[kind * J0 * SJ + j0 + J0 * pair]
   __syncthreads();
-  const int nacc = 2 * J0 * SJ;
+  const int nacc = KINDS * J0 * SJ;
   for (int w = 0; w < nwarps; ++w) {
     if (warp == w) {
       for (int j = 0; j < J0; ++j) {
@@ -856,11 +884,15 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
         for (int i = 0; i < SPL; ++i) {
           if (on[i]) {
             const T* x1 = rs + ((size_t)(0 * J0 + j) * SPL + i) * 64 + lane;
-            const T* x2 = rs + ((size_t)(1 * J0 + j) * SPL + i) * 64 + lane;
-            const int e1 = j + J0 * (lane + 32 * i), e2 = J0 * SJ + e1;
-            const double v1 = CoreAcc<T>::value(x1[0], x1[32]), v2 = CoreAcc<T>::value(x2[0], x2[32]);
+            const int e1 = j + J0 * (lane + 32 * i);
+            const double v1 = CoreAcc<T>::value(x1[0], x1[32]);
             red[e1] = w == 0 ? v1 : red[e1] + v1;
-            red[e2] = w == 0 ? v2 : red[e2] + v2;
+            if constexpr (DIAG) {
+              const T* x2 = rs + ((size_t)(1 * J0 + j) * SPL + i) * 64 + lane;
+              const int e2 = J0 * SJ + e1;
+              const double v2 = CoreAcc<T>::value(x2[0], x2[32]);
+              red[e2] = w == 0 ? v2 : red[e2] + v2;
+            }
           }
         }
       }
@@ -871,15 +903,34 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
 }
 
 // Delta and Resp of the group's core elements: lin = j0 + J0 (j1 + J1 s).
+// diag M of the element: sums[n + e] when the stats pass formed it, else the diagonal of
+// its block Gram (block (s, j1 / m), local index j0 + J0 (j1 - q0)).
+struct DiagSrc {
+  const double* gram;  // NULL: diag in sums
+  int m, nq0;
+  int64_t nmmax;
+};
+
 template <typename T>
 __global__ void core_resp_kernel(DevModel<T> M, int J0, int J1, int64_t s0, int SJ, const double* __restrict__ sums,
-                                 const double* __restrict__ stats, double* __restrict__ delta, double* __restrict__ resp) {
+                                 DiagSrc ds, const double* __restrict__ stats, double* __restrict__ delta,
+                                 double* __restrict__ resp) {
   const double xx = stats[1], re = stats[4];
   const int n = J0 * SJ;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const int64_t lin = (int64_t)J0 * J1 * s0 + e;  // e = j0 + J0 * (j1 + J1 * si)
     const double gv = (double)M.G[lin];
-    const double dl = 2.0 * gv * sums[e] + gv * gv * sums[n + e];
+    double dg;
+    if (ds.gram) {
+      const int j0 = e % J0, j1 = (e / J0) % J1;
+      const int64_t sfx = s0 + e / (J0 * J1);
+      const int qc = j1 / ds.m, q0 = qc * ds.m, mq = min(ds.m, J1 - q0), b = J0 * mq;
+      const int kk = j0 + J0 * (j1 - q0);
+      dg = ds.gram[(sfx * ds.nq0 + qc) * ds.nmmax + sym_index(kk, kk, b)];
+    } else {
+      dg = sums[n + e];
+    }
+    const double dl = 2.0 * gv * sums[e] + gv * gv * dg;
     delta[lin] = dl;
     if (resp) resp[lin] = re > 0.0 ? (sqrt(fmax(re * re + dl / xx, 0.0)) - re) / re : 0.0;
   }
@@ -892,9 +943,12 @@ struct CorePlan {
   int64_t nblocks;
   int bmax, nmmax;
   int nX, nYmax, SgMax, Pmax;  // gram groups
-  int SgStats, SJ;             // stats groups
+  int SgStats, SJ;             // stats groups (g and diag M)
+  int SgStatsG, SJG;           // stats groups (g alone, diag M from the block Grams)
   int64_t slots;
 };
+
+static int64_t stats_nacc_max(const struct CorePlan& c);
 
 static CorePlan core_plan(const int32_t* J, int N, int64_t nnz, int64_t cap0) {
   CorePlan c{};
@@ -916,12 +970,21 @@ static CorePlan core_plan(const int32_t* J, int N, int64_t nnz, int64_t cap0) {
     c.Pmax = std::max(c.Pmax, c.SgMax * nY);
   }
   // stats: 32 * stats_spl streams (j1, s) per group
-  const int streams = 32 * stats_spl(jn_bucket(c.J0));
+  const int streams = 32 * stats_spl(jn_bucket(c.J0), true);
   const int sg = (int)std::max<int64_t>(1, std::min<int64_t>(c.S, streams / c.J1));
   c.SgStats = sg;
   c.SJ = sg * c.J1;
+  const int streams_g = 32 * stats_spl(jn_bucket(c.J0), false);
+  const int sgg = (int)std::max<int64_t>(1, std::min<int64_t>(c.S, streams_g / c.J1));
+  c.SgStatsG = sgg;
+  c.SJG = sgg * c.J1;
   c.slots = cap0 + ceil_div(std::max<int64_t>(nnz, 1), kCoreTask) + 1;
   return c;
+}
+
+// outputs of one stats group, at most: 2 J0 SJ with diag, J0 SJG without
+static int64_t stats_nacc_max(const CorePlan& c) {
+  return std::max<int64_t>((int64_t)2 * c.J0 * c.SJ, (int64_t)c.J0 * c.SJG);
 }
 
 size_t core_scratch_bytes(const vest_model* m, int64_t nnz, int64_t cap0, size_t* y_bytes, size_t* gram_bytes,
@@ -936,7 +999,8 @@ size_t core_scratch_bytes(const vest_model* m, int64_t nnz, int64_t cap0, size_t
   *gram_bytes = align_up(std::max((size_t)c.nblocks * c.nmmax, (size_t)2 * c.J0 * c.SJ) * 8);
   const size_t gemm = (size_t)kGramKSplit * c.nX * c.Pmax * 8;
   const size_t gp = (size_t)(kCorePassCtas + kMergeGroups) * kCoreMaxB * 8;
-  const size_t st = (size_t)(kCorePassCtas + kMergeGroups) * 2 * c.J0 * c.SJ * 8;
+  // per-CTA partials, the merge's groups and the merged sums of one stats group
+  const size_t st = (size_t)(kCorePassCtas + kMergeGroups + 1) * stats_nacc_max(c) * 8;
   *part_bytes = align_up(std::max({gemm, gp, st}));
   return *y_bytes + *gram_bytes + *part_bytes;
 }
@@ -965,11 +1029,11 @@ static vest_status launch_gram(const DevModel<T>& M, const DevMode<T>& csr, cons
 // Shared memory of the stats pass; *red_off receives the offset of the FP64 warp
 // reduction: inside the staging region when it fits there, else behind everything.
 template <typename T>
-static size_t smem_stats(int J0, int J1, int Sg, int SJ, int nwarps, size_t* red_off = nullptr) {
-  const int spl = stats_spl(jn_bucket(J0));
-  const size_t pass = (size_t)nwarps * (stats_stage_elems(J0, J1, Sg) + stats_run_elems(J0, spl)) * sizeof(T) +
+static size_t smem_stats(int J0, int J1, int Sg, int SJ, int nwarps, bool diag, size_t* red_off = nullptr) {
+  const int spl = stats_spl(jn_bucket(J0), diag), kinds = diag ? 2 : 1;
+  const size_t pass = (size_t)nwarps * (stats_stage_elems(J0, J1, Sg) + stats_run_elems(J0, spl, kinds)) * sizeof(T) +
                       (size_t)nwarps * 32 * 4;
-  const size_t red = (size_t)2 * J0 * SJ * 8;
+  const size_t red = (size_t)kinds * J0 * SJ * 8;
   const bool inside = red <= (size_t)nwarps * stats_stage_elems(J0, J1, Sg) * sizeof(T);
   if (red_off) *red_off = inside ? 0 : align_up(pass, 16);
   return inside ? pass : align_up(pass, 16) + red;
@@ -977,16 +1041,16 @@ static size_t smem_stats(int J0, int J1, int Sg, int SJ, int nwarps, size_t* red
 
 // Warps per CTA of the stats pass: 8 unless the shared memory would exceed 200 KB.
 template <typename T>
-static int stats_warps(int J0, int J1, int Sg, int SJ) {
+static int stats_warps(int J0, int J1, int Sg, int SJ, bool diag) {
   int w = 8;
-  while (w > 1 && smem_stats<T>(J0, J1, Sg, SJ, w) > 200 * 1024) w /= 2;
+  while (w > 1 && smem_stats<T>(J0, J1, Sg, SJ, w, diag) > 200 * 1024) w /= 2;
   return w;
 }
 
 template <typename T, int J0B>
 static vest_status launch_stats(const DevModel<T>& M, const DevMode<T>& csr, const T* r, const T* A0c,
-                                const StatsArgs& a, int grid, int nwarps, size_t smem, cudaStream_t s) {
-  auto kern = core_stats_kernel<T, J0B>;
+                                const StatsArgs& a, bool diag, int grid, int nwarps, size_t smem, cudaStream_t s) {
+  auto kern = diag ? core_stats_kernel<T, J0B, true> : core_stats_kernel<T, J0B, false>;
   VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<grid, 32 * nwarps, smem, s>>>(M, csr, r, A0c, a);
   VEST_LAUNCH("core_stats_kernel");
@@ -1163,14 +1227,19 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
 template <typename T>
 vest_status core_responsibility(const vest_index* ix, const vest_model* mdl, const T* resid_csr0, const double* stats,
                                 double* delta_core, double* resp_core, char* scratch, const ScratchPlan& plan,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool grams_valid) {
   const DevModel<T> M = dev_model<T>(mdl);
   if (M.N < 2) return fail(VEST_ERR_UNSUPPORTED, "order < 2");
   const CorePlan c = core_plan(M.J, M.N, ix->nnz, ix->mode[0].cap);
   const CoreBufs bf = core_bufs(ix, mdl, scratch, plan);
   const DevMode<T> csr = dev_mode<T>(ix, 0);
   const int64_t ntasks = ceil_div(ix->nnz, kCoreTask);
-  double* sums = bf.gram;  // reuse the gram region: [2 * J0 * SJ]
+  // right after a core sweep with these factors the block Grams hold diag M: the stats pass forms g alone
+  const bool diag = !grams_valid;
+  const int sgs = diag ? c.SgStats : c.SgStatsG;
+  const DiagSrc ds{diag ? nullptr : bf.gram, c.m, c.nq0, c.nmmax};
+  const int64_t nmax = stats_nacc_max(c);
+  double* sums = bf.part + (size_t)(kCorePassCtas + kMergeGroups) * nmax;
   T* A0c = reinterpret_cast<T*>(bf.Y);  // the per-piece gram region is free here: a0 per non-empty row
   if (ix->nnz > 0) {
     core_a0c_kernel<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->mode[0].cap * c.J0, 256),
@@ -1178,34 +1247,34 @@ vest_status core_responsibility(const vest_index* ix, const vest_model* mdl, con
                          256, 0, s>>>(M, csr.nzrow, csr.nnzrows, c.J0, A0c);
     VEST_LAUNCH("core_a0c_kernel");
   }
-  for (int64_t s0 = 0; s0 < c.S; s0 += c.SgStats) {
+  for (int64_t s0 = 0; s0 < c.S; s0 += sgs) {
     StatsArgs a{};
     a.J0 = c.J0;
     a.J1 = c.J1;
     a.s0 = s0;
-    a.Sg = (int)std::min<int64_t>(c.SgStats, c.S - s0);
+    a.Sg = (int)std::min<int64_t>(sgs, c.S - s0);
     a.SJ = a.Sg * c.J1;
     a.nnz = ix->nnz;
     a.ntasks = ntasks;
     a.part = bf.part;
-    const int nacc = 2 * c.J0 * a.SJ;
+    const int nacc = (diag ? 2 : 1) * c.J0 * a.SJ;
     if (ix->nnz > 0) {
-      const int nwarps = stats_warps<T>(c.J0, c.J1, a.Sg, a.SJ);
+      const int nwarps = stats_warps<T>(c.J0, c.J1, a.Sg, a.SJ, diag);
       const int nctas = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ntasks, nwarps), kCorePassCtas));
-      const size_t smem = smem_stats<T>(c.J0, c.J1, a.Sg, a.SJ, nwarps, &a.red_off);
+      const size_t smem = smem_stats<T>(c.J0, c.J1, a.Sg, a.SJ, nwarps, diag, &a.red_off);
       switch (jn_bucket(c.J0)) {
-        case 4: VEST_TRY(launch_stats<T, 4>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
-        case 8: VEST_TRY(launch_stats<T, 8>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
-        case 10: VEST_TRY(launch_stats<T, 10>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
-        case 12: VEST_TRY(launch_stats<T, 12>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
-        case 16: VEST_TRY(launch_stats<T, 16>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
-        default: VEST_TRY(launch_stats<T, 32>(M, csr, resid_csr0, A0c, a, nctas, nwarps, smem, s)); break;
+        case 4: VEST_TRY(launch_stats<T, 4>(M, csr, resid_csr0, A0c, a, diag, nctas, nwarps, smem, s)); break;
+        case 8: VEST_TRY(launch_stats<T, 8>(M, csr, resid_csr0, A0c, a, diag, nctas, nwarps, smem, s)); break;
+        case 10: VEST_TRY(launch_stats<T, 10>(M, csr, resid_csr0, A0c, a, diag, nctas, nwarps, smem, s)); break;
+        case 12: VEST_TRY(launch_stats<T, 12>(M, csr, resid_csr0, A0c, a, diag, nctas, nwarps, smem, s)); break;
+        case 16: VEST_TRY(launch_stats<T, 16>(M, csr, resid_csr0, A0c, a, diag, nctas, nwarps, smem, s)); break;
+        default: VEST_TRY(launch_stats<T, 32>(M, csr, resid_csr0, A0c, a, diag, nctas, nwarps, smem, s)); break;
       }
       VEST_TRY(vec_merge(bf.part, nctas, nacc, sums, bf.part + (size_t)kCorePassCtas * nacc, s));
     } else {
       VEST_CUDA(cudaMemsetAsync(sums, 0, (size_t)nacc * 8, s));
     }
-    core_resp_kernel<T><<<(unsigned)ceil_div(c.J0 * a.SJ, 256), 256, 0, s>>>(M, c.J0, c.J1, s0, a.SJ, sums, stats,
+    core_resp_kernel<T><<<(unsigned)ceil_div(c.J0 * a.SJ, 256), 256, 0, s>>>(M, c.J0, c.J1, s0, a.SJ, sums, ds, stats,
                                                                               delta_core, resp_core);
     VEST_LAUNCH("core_resp_kernel");
   }
@@ -1217,8 +1286,8 @@ template vest_status sweep_core_impl<float>(const vest_index*, const vest_model*
 template vest_status sweep_core_impl<double>(const vest_index*, const vest_model*, int, double, char*,
                                              const ScratchPlan&, cudaStream_t, double*);
 template vest_status core_responsibility<float>(const vest_index*, const vest_model*, const float*, const double*,
-                                                double*, double*, char*, const ScratchPlan&, cudaStream_t);
+                                                double*, double*, char*, const ScratchPlan&, cudaStream_t, bool);
 template vest_status core_responsibility<double>(const vest_index*, const vest_model*, const double*, const double*,
-                                                 double*, double*, char*, const ScratchPlan&, cudaStream_t);
+                                                 double*, double*, char*, const ScratchPlan&, cudaStream_t, bool);
 
 }  // namespace vest

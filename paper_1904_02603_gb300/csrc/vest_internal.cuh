@@ -184,10 +184,11 @@ template <typename T>
 vest_status loss_finish(const vest_model* m, int reg, double lambda, int nl, double* out, char* scratch,
                         const ScratchPlan& plan, cudaStream_t s);
 int loss_ctas();
+// grams_valid: a core sweep with the current factors ran last, so its block Grams hold diag M.
 template <typename T>
 vest_status core_responsibility(const vest_index* ix, const vest_model* m, const T* resid_csr0,
                                 const double* stats, double* delta_core, double* resp_core, char* scratch,
-                                const ScratchPlan& plan, cudaStream_t s);
+                                const ScratchPlan& plan, cudaStream_t s, bool grams_valid = false);
 template <typename T>
 vest_status prune_impl(const vest_model* m, double* const* delta_factor, const double* delta_core, double pr,
                        int count_mode, int threshold_mode, double tau, int64_t* n_pruned, char* scratch,
