@@ -391,7 +391,7 @@ __global__ void core_a0c_kernel(DevModel<T> M, const int32_t* __restrict__ nzrow
 // suffix weights, u, and the head lanes' a0 rows from A0c) are issued together
 // after the coalesced index loads.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) core_g_pass_kernel(DevModel<T> M, DevMode<T> csr, T* r, const T* __restrict__ U,
+__global__ void __launch_bounds__(256, 3) core_g_pass_kernel(DevModel<T> M, DevMode<T> csr, T* r, const T* __restrict__ U,
                                                           const T* __restrict__ A0c, GPassArgs a) {
   constexpr int kPer = kCoreMaxB / 32;
   __shared__ T sh[8][kCoreMaxM];
@@ -406,60 +406,28 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) core_g_pass_kerne
   for (int i = 0; i < kPer; ++i) as[i] = ac[i] = T(0);
   const int64_t nchunks = ceil_div(a.nnz, 32);
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp, nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  // Software pipeline over the warp's chunks: while chunk ch is processed, the gathers of
-  // chunk ch + nw (a1 row, u row, suffix weights) and the coalesced loads of chunk ch + 2 nw
-  // (row, mode-1 index, mode-2 index when N = 3, r) are in flight.
+  // the coalesced loads of a chunk (row, mode-1 index, mode-2 index when N = 3, r) are
+  // issued one chunk ahead
   const bool n3 = M.N == 3;
-  struct Idx {
-    int k, i1, i2;
-    T rv;
-  };
-  struct Val {
-    T v[kCoreMaxM], u[kCoreMaxM];
-    T c, cp;
-  };
-  auto load_idx = [&](int64_t ch, Idx& x) {
+  int nk = 0, ni1 = 0, ni2 = 0;
+  T nrv = T(0);
+  auto prefetch = [&](int64_t ch) {
     const int64_t p = ch * 32 + lane;
     if (ch < nchunks && p < a.nnz) {
-      x.k = csr.rowk[p];
-      x.i1 = csr.oidx[p];
-      if (n3) x.i2 = csr.oidx[a.nnz + p];
-      x.rv = r[p];
+      nk = csr.rowk[p];
+      ni1 = csr.oidx[p];
+      if (n3) ni2 = csr.oidx[a.nnz + p];
+      nrv = r[p];
     }
   };
-  auto load_val = [&](int64_t ch, const Idx& x, Val& g) {
-    const int64_t p = ch * 32 + lane;
-    if (ch < nchunks && p < a.nnz) {
-      const T* a1 = M.A[1] + (int64_t)x.i1 * a.J1 + a.cur.q0;
-#pragma unroll
-      for (int q = 0; q < kCoreMaxM; ++q)
-        if (q < m) g.v[q] = a1[q];
-      if (a.has_prev) {
-        const T* u = U + (int64_t)x.k * kCoreMaxM;
-#pragma unroll
-        for (int q = 0; q < kCoreMaxM; ++q)
-          if (q < mp) g.u[q] = u[q];
-        if (n3) g.cp = M.A[2][(int64_t)x.i2 * M.J[2] + a.prev.s];
-        else suffix_weights<T>(M, csr.oidx, a.nnz, p, a.prev.s, 1, &g.cp, 1);
-      }
-      if (n3) g.c = M.A[2][(int64_t)x.i2 * M.J[2] + a.cur.s];
-      else suffix_weights<T>(M, csr.oidx, a.nnz, p, a.cur.s, 1, &g.c, 1);
-    }
-  };
-  Idx xn{0, 0, 0, T(0)}, xnn{0, 0, 0, T(0)};
-  Val gn;
-  load_idx(gw, xn);
-  load_val(gw, xn, gn);
-  load_idx(gw + nw, xnn);
+  prefetch(gw);
   for (int64_t ch = gw; ch < nchunks; ch += nw) {
     const int64_t p = ch * 32 + lane;
     const bool valid = p < a.nnz;
-    const Idx xc = xn;
-    const Val gc = gn;
-    xn = xnn;
-    load_val(ch + nw, xn, gn);
-    load_idx(ch + 2 * nw, xnn);
-    const int k = valid ? xc.k : -1 - lane;
+    const int k = valid ? nk : -1 - lane;
+    const int i1 = ni1, i2 = ni2;
+    const T rv0 = nrv;
+    prefetch(ch + nw);
     const int kup = __shfl_up_sync(0xffffffffu, k, 1);
     const bool head = valid && (lane == 0 || kup != k);
     T h[kCoreMaxM];
@@ -471,20 +439,31 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) core_g_pass_kerne
       for (int j = 0; j < J0; ++j) sa[lane * J0 + j] = a0[j];
     }
     if (valid) {
-      T rv = xc.rv;
+      const T* a1 = M.A[1] + (int64_t)i1 * a.J1;
+      T rv = rv0;
+      T v[kCoreMaxM];
+#pragma unroll
+      for (int q = 0; q < kCoreMaxM; ++q)
+        if (q < m) v[q] = a1[a.cur.q0 + q];
       if (a.has_prev) {
-        const T* a1p = M.A[1] + (int64_t)xc.i1 * a.J1 + a.prev.q0;
+        T cp;
+        if (n3) cp = M.A[2][(int64_t)i2 * M.J[2] + a.prev.s];
+        else suffix_weights<T>(M, csr.oidx, a.nnz, p, a.prev.s, 1, &cp, 1);
+        const T* u = U + (int64_t)k * kCoreMaxM;
         T acc = T(0);
 #pragma unroll
         for (int q = 0; q < kCoreMaxM; ++q)
-          if (q < mp) acc += (same_q ? gc.v[q] : a1p[q]) * gc.u[q];
-        rv -= gc.cp * acc;
+          if (q < mp) acc += (same_q ? v[q] : a1[a.prev.q0 + q]) * u[q];
+        rv -= cp * acc;
         r[p] = rv;
       }
-      const T rc = rv * gc.c;
+      T c;
+      if (n3) c = M.A[2][(int64_t)i2 * M.J[2] + a.cur.s];
+      else suffix_weights<T>(M, csr.oidx, a.nnz, p, a.cur.s, 1, &c, 1);
+      const T rc = rv * c;
 #pragma unroll
       for (int q = 0; q < kCoreMaxM; ++q)
-        if (q < m) h[q] = rc * gc.v[q];
+        if (q < m) h[q] = rc * v[q];
     }
     // segmented suffix sums: lane l ends with the sum over its row from l to the chunk end
 #pragma unroll

@@ -3,7 +3,7 @@
 // (Delta, linear index) and the first k = floor(pr * #candidates) (or
 // floor(pr * size)) are marked and zeroed.  The k-th pair is found by a radix
 // select on the 96-bit composite (order-preserving 64-bit key of Delta, with
-// -0 read as +0; 32-bit index): twelve histogram passes of 8-bit digits, most
+// -0 read as +0; 32-bit index): nine histogram passes of 11-bit digits, most
 // significant first, each narrowing the prefix of the k-th pair; the last CTA
 // of a pass (atomic ticket) picks the digit.  A final pass marks every
 // candidate whose pair is not above the selected one.  Integer work only after
@@ -14,9 +14,9 @@
 
 namespace vest {
 
-constexpr int kSelBits = 8;
+constexpr int kSelBits = 11;
 constexpr int kSelBins = 1 << kSelBits;
-constexpr int kSelPasses = 12;  // 96 bits in 8-bit digits
+constexpr int kSelPasses = 9;  // 96 bits: 8 x 11 + 8
 
 struct SelectState {
   unsigned long long pkey;  // selected prefix: key bits
@@ -221,8 +221,7 @@ vest_status prune_impl(const vest_model* m, double* const* delta_factor, const d
     T* val = core ? M.G : M.A[seg];
     const double* dl = core ? delta_core : delta_factor[seg];
     int64_t* np = n_pruned ? n_pruned + seg : nullptr;
-    // few CTAs of many elements each: fewer histogram flushes into the 256 global bins
-    const int grid = std::max(1, std::min<int>((int)ceil_div(size, 4096), num_sms() * 2));
+    const int grid = std::max(1, std::min<int>((int)ceil_div(size, 256), num_sms() * 4));
     if (size > 0xFFFFFFFFll) return fail(VEST_ERR_UNSUPPORTED, "prune: a segment holds 2^32 elements or more");
     if (threshold_mode) {
       VEST_CUDA(cudaMemsetAsync(cnt, 0, sizeof(*cnt), s));
