@@ -32,7 +32,11 @@ constexpr int kCoreTask = 256;
 constexpr int kCoreMaxB = 128;
 constexpr int kCoreMaxM = 10;
 constexpr int kGramKSplit = 64;     // fixed: reduction order does not depend on the device
-constexpr int kCorePassCtas = 1216;  // fixed likewise (8 per SM on 152 SMs)
+// Fixed CTA counts (the order of every sum is then the same on any device), chosen as
+// whole waves on 152 SMs: the stats pass holds 2 CTAs per SM (1216 = 4 waves), the g pass 3
+// (1368 = 3 waves).
+constexpr int kCorePassCtas = 1216;
+constexpr int kGPassCtas = 1368;
 
 struct CoreBlock {
   int64_t s;  // suffix linear index over modes >= 2
@@ -977,7 +981,7 @@ size_t core_scratch_bytes(const vest_model* m, int64_t nnz, int64_t cap0, size_t
   // the gram region also holds the responsibility sums (2 * J0 * SJ doubles)
   *gram_bytes = align_up(std::max((size_t)c.nblocks * c.nmmax, (size_t)2 * c.J0 * c.SJ) * 8);
   const size_t gemm = (size_t)kGramKSplit * c.nX * c.Pmax * 8;
-  const size_t gp = (size_t)(kCorePassCtas + kMergeGroups) * kCoreMaxB * 8;
+  const size_t gp = (size_t)(kGPassCtas + kMergeGroups) * kCoreMaxB * 8;
   // per-CTA partials, the merge's groups and the merged sums of one stats group
   const size_t st = (size_t)(kCorePassCtas + kMergeGroups + 1) * stats_nacc_max(c) * 8;
   *part_bytes = align_up(std::max({gemm, gp, st}));
@@ -1151,7 +1155,7 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
   // the per-piece gram region is free again: u and the a0 row per non-empty row
   T* U = reinterpret_cast<T*>(bf.Y);
   T* A0c = U + (size_t)(ix->mode[0].cap + 1) * kCoreMaxM;
-  const int nctas_g = kCorePassCtas;
+  const int nctas_g = kGPassCtas;
   const size_t gsm = (size_t)8 * 32 * c.J0 * sizeof(T);
   if (ix->nnz > 0) {
     core_a0c_kernel<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->mode[0].cap * c.J0, 256),
@@ -1176,7 +1180,7 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
         }
         core_g_pass_kernel<T><<<nctas_g, 256, gsm, s>>>(M, csr, r0, U, A0c, a);
         VEST_LAUNCH("core_g_pass_kernel");
-        VEST_TRY(vec_merge(bf.part, nctas_g, blk.b, gvec, bf.part + (size_t)kCorePassCtas * kCoreMaxB, s));
+        VEST_TRY(vec_merge(bf.part, nctas_g, blk.b, gvec, bf.part + (size_t)kGPassCtas * kCoreMaxB, s));
       } else {
         VEST_CUDA(cudaMemsetAsync(gvec, 0, (size_t)blk.b * 8, s));
       }

@@ -353,7 +353,7 @@ constexpr size_t kSmemBudget = 200 * 1024;
 constexpr size_t kSmemMax = 227 * 1024;
 constexpr size_t kAccBudget = 32 * 1024;
 constexpr int kTask = 256;
-constexpr int64_t kSweepBlocks = 2432;
+constexpr int64_t kSweepBlocks = 3040;  // fixed (sum order device-independent): 4 waves of 5 blocks on 152 SMs
 
 template <typename T>
 static int pieces_per_round(int P) {
