@@ -281,6 +281,35 @@ vest_status vest_responsibility(const vest_index* ix, const vest_model* m, doubl
   return core_responsibility<float>(ix, m, r0, stats, delta_core, resp_core, sc, plan, s);
 }
 
+// One iteration of Algorithm 2 in two halves.  The first sweeps (factors unless told
+// otherwise, then the core) and leaves the residual of the swept model in the scratch,
+// writing its loss; the second takes the responsibility from that residual (and diag M
+// from the core sweep's block Grams) and prunes.  Nothing may change the model between them.
+static vest_status iteration_sweeps(const vest_index* ix, vest_model* m, int32_t reg, double lambda,
+                                    int32_t factor_sweep, double* loss, void* scratch, size_t scratch_bytes,
+                                    const ScratchPlan& plan, void* stream) {
+  char* sc = static_cast<char*>(scratch);
+  const cudaStream_t s = as_stream(stream);
+  if (factor_sweep) VEST_TRY(vest_sweep_factors(ix, m, reg, lambda, -1, scratch, scratch_bytes, stream));
+  if (m->dtype == VEST_F64) return sweep_core_impl<double>(ix, m, reg, lambda, sc, plan, s, loss);
+  return sweep_core_impl<float>(ix, m, reg, lambda, sc, plan, s, loss);
+}
+
+static vest_status iteration_prune(const vest_index* ix, vest_model* m, const double* loss, double pr,
+                                   int32_t count_mode, double* const* delta_factor, double* delta_core,
+                                   int64_t* n_pruned, char* sc, const ScratchPlan& plan, cudaStream_t s) {
+  if (m->dtype == VEST_F64) {
+    const double* r0 = reinterpret_cast<const double*>(sc + plan.off_resid);
+    VEST_TRY(responsibility_factors<double>(ix, m, loss, delta_factor, nullptr, sc, plan, s));
+    VEST_TRY(core_responsibility<double>(ix, m, r0, loss, delta_core, nullptr, sc, plan, s, true));
+    return prune_impl<double>(m, delta_factor, delta_core, pr, count_mode, 0, 0.0, n_pruned, sc, plan, s);
+  }
+  const float* r0 = reinterpret_cast<const float*>(sc + plan.off_resid);
+  VEST_TRY(responsibility_factors<float>(ix, m, loss, delta_factor, nullptr, sc, plan, s));
+  VEST_TRY(core_responsibility<float>(ix, m, r0, loss, delta_core, nullptr, sc, plan, s, true));
+  return prune_impl<float>(m, delta_factor, delta_core, pr, count_mode, 0, 0.0, n_pruned, sc, plan, s);
+}
+
 vest_status vest_iteration(const vest_index* ix, vest_model* m, int32_t reg, double lambda, double pr,
                            int32_t count_mode, int32_t factor_sweep, double* loss, double* const* delta_factor,
                            double* delta_core, int64_t* n_pruned, void* scratch, size_t scratch_bytes, void* stream) {
@@ -296,25 +325,10 @@ vest_status vest_iteration(const vest_index* ix, vest_model* m, int32_t reg, dou
       if (!delta_factor[n]) return fail(VEST_ERR_INVALID, "delta_factor entry is NULL");
   ScratchPlan plan;
   VEST_TRY(check_scratch(ix, m, scratch, scratch_bytes, &plan));
-  char* sc = static_cast<char*>(scratch);
-  const cudaStream_t s = as_stream(stream);
-  if (factor_sweep) VEST_TRY(vest_sweep_factors(ix, m, reg, lambda, -1, scratch, scratch_bytes, stream));
-  if (m->dtype == VEST_F64) {
-    VEST_TRY(sweep_core_impl<double>(ix, m, reg, lambda, sc, plan, s, loss));
-    if (!resp) return VEST_OK;
-    const double* r0 = reinterpret_cast<const double*>(sc + plan.off_resid);
-    VEST_TRY(responsibility_factors<double>(ix, m, loss, delta_factor, nullptr, sc, plan, s));
-    VEST_TRY(core_responsibility<double>(ix, m, r0, loss, delta_core, nullptr, sc, plan, s, true));
-  } else {
-    VEST_TRY(sweep_core_impl<float>(ix, m, reg, lambda, sc, plan, s, loss));
-    if (!resp) return VEST_OK;
-    const float* r0 = reinterpret_cast<const float*>(sc + plan.off_resid);
-    VEST_TRY(responsibility_factors<float>(ix, m, loss, delta_factor, nullptr, sc, plan, s));
-    VEST_TRY(core_responsibility<float>(ix, m, r0, loss, delta_core, nullptr, sc, plan, s, true));
-  }
-  if (m->dtype == VEST_F64)
-    return prune_impl<double>(m, delta_factor, delta_core, pr, count_mode, 0, 0.0, n_pruned, sc, plan, s);
-  return prune_impl<float>(m, delta_factor, delta_core, pr, count_mode, 0, 0.0, n_pruned, sc, plan, s);
+  VEST_TRY(iteration_sweeps(ix, m, reg, lambda, factor_sweep, loss, scratch, scratch_bytes, plan, stream));
+  if (!resp) return VEST_OK;
+  return iteration_prune(ix, m, loss, pr, count_mode, delta_factor, delta_core, n_pruned,
+                         static_cast<char*>(scratch), plan, as_stream(stream));
 }
 
 static vest_status prune_checked(vest_model* m, double* const* delta_factor, const double* delta_core, double pr,
@@ -423,10 +437,9 @@ vest_status vest_autosearch(const vest_index* ix, vest_model* m, const vest_para
   (void)gs;
   bool pruning = true;
   for (int it = 1; it <= p->max_iter; ++it) {
-    VEST_TRY(vest_sweep_factors(ix, m, p->reg, p->lambda, -1, scratch, scratch_bytes, stream));
-    VEST_TRY(vest_sweep_core(ix, m, p->reg, p->lambda, scratch, scratch_bytes, stream));
-    if (m->dtype == VEST_F64) VEST_TRY(loss_impl<double>(ix, m, p->reg, p->lambda, loss, nullptr, nullptr, sc, plan, s));
-    else VEST_TRY(loss_impl<float>(ix, m, p->reg, p->lambda, loss, nullptr, nullptr, sc, plan, s));
+    // the sweeps leave the residual of the swept model in the scratch: the loss and, when
+    // this iteration prunes, the responsibility read it instead of recomputing B
+    VEST_TRY(iteration_sweeps(ix, m, p->reg, p->lambda, 1, loss, scratch, scratch_bytes, plan, stream));
     double hl[5];
     VEST_CUDA(cudaMemcpyAsync(hl, loss, sizeof(hl), cudaMemcpyDeviceToHost, s));
     VEST_CUDA(cudaStreamSynchronize(s));
@@ -448,8 +461,7 @@ vest_status vest_autosearch(const vest_index* ix, vest_model* m, const vest_para
       if (!pruning) {
         rep->stop_iter = it;
       } else {
-        VEST_TRY(vest_responsibility(ix, m, dfac, dcore, nullptr, nullptr, scratch, scratch_bytes, stream));
-        VEST_TRY(prune_checked(m, dfac, dcore, pr, p->count_mode, 0, 0.0, nullptr, sc, plan, s));
+        VEST_TRY(iteration_prune(ix, m, loss, pr, p->count_mode, dfac, dcore, nullptr, sc, plan, s));
         rep->pr_hist[h] = pr;
       }
     }

@@ -13,7 +13,7 @@
 namespace vest {
 
 constexpr int kLossTask = 256;
-constexpr int kLossCtas = 1216;
+constexpr int kLossCtas = 760;  // fixed (sum order device-independent): one wave of 5 CTAs on 152 SMs
 constexpr int kRegCtas = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -76,10 +76,15 @@ __global__ void __launch_bounds__(kLossTask / E, (delta_min_blocks<T, JN, JF, E>
     if ((int)threadIdx.x < cnt) {
       const T* rowf[E];
       SlowRows sr[E];
+      int64_t i0[E];  // mode-0 row of each entry, resolved before the contraction
+      T xv[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int q = threadIdx.x + e * blockDim.x;
-        rowf[e] = gather_rows<T, NSLOW>(M, r, csr.oidx, nnz, t0 + (q < cnt ? q : (int)threadIdx.x), sr[e]);
+        const int64_t pe = t0 + (q < cnt ? q : (int)threadIdx.x);
+        rowf[e] = gather_rows<T, NSLOW>(M, r, csr.oidx, nnz, pe, sr[e]);
+        i0[e] = csr.nzrow[csr.rowk[pe]];
+        xv[e] = csr.val[pe];
       }
       T d[E][JN];
       compute_delta_multi<T, JN, JF, NSLOW, E>(d, g, a.onz, r.n_outer, r.Jf, rowf, sr, r.nslow);
@@ -88,13 +93,12 @@ __global__ void __launch_bounds__(kLossTask / E, (delta_min_blocks<T, JN, JF, E>
         const int q = threadIdx.x + e * blockDim.x;
         if (q >= cnt) continue;
         const int64_t p = t0 + q;
-        const int64_t i0 = csr.nzrow[csr.rowk[p]];
-        const T* a0 = M.A[0] + i0 * J0;
+        const T* a0 = M.A[0] + i0[e] * J0;
         T b = T(0);
 #pragma unroll
         for (int j = 0; j < JN; ++j)
           if (j < J0) b += __ldg(a0 + j) * d[e][j];
-        const T x = csr.val[p];
+        const T x = xv[e];
         const T res = x - b;
         if (resid_csr0) resid_csr0[p] = res;
         if (resid_coo) resid_coo[csr.perm[p]] = res;
