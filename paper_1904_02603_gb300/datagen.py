@@ -160,6 +160,29 @@ def planted_values(idx: np.ndarray, planted: ModelState, noise: float, rng) -> n
     return x
 
 
+def planted_values_on(device, idx: np.ndarray, planted: ModelState, noise: float, rng) -> np.ndarray:
+    """planted_values with the per-term products on a torch device (same terms, same order, FP64:
+    the same numbers), for generating large batches of inputs quickly."""
+    import torch
+    ranks = planted.ranks
+    N = len(ranks)
+    it = [torch.from_numpy(np.ascontiguousarray(idx[n]).astype(np.int64)).to(device) for n in range(N)]
+    cols = [torch.from_numpy(np.ascontiguousarray(f.T)).to(device) for f in planted.factors]
+    x = torch.zeros(idx.shape[1], dtype=torch.float64, device=device)
+    for b in np.nonzero(planted.core)[0]:
+        rest = int(b)
+        term = torch.full((idx.shape[1],), float(planted.core[b]), dtype=torch.float64, device=device)
+        for n in range(N):
+            j = rest % ranks[n]
+            rest //= ranks[n]
+            term *= cols[n][j][it[n]]
+        x += term
+    out = x.cpu().numpy()
+    if noise > 0:
+        out = out + rng.normal(0.0, noise, size=out.shape)
+    return out
+
+
 def random_init(dims, ranks, seed: int, dtype=np.float64) -> ModelState:
     """Algorithm 2, first line: every core and factor element drawn U(0,1)."""
     rng = np.random.default_rng(seed)
@@ -208,8 +231,29 @@ WORKLOADS = {
 }
 
 
-def make(w: Workload | str, **overrides):
-    """Returns (tensor, initial model state, planted model) for a workload."""
+def batch_workloads(count: int = 256, seed: int = 1003, init_seed: int = 2003) -> list:
+    """The batched configuration: independent jobs of order 3 or 4 (equal odds), mode sizes
+    log-uniform in [50, 5000], nnz log-uniform in [1e3, 1e6] capped at half the tensor, ranks
+    uniform in 3..10 per mode, planted sparse Tucker values (core 20 %, factors 40 %, noise
+    0.01), FP32, L_F with lambda 0.01.  Job j draws its data from seed * 1000 + j and its
+    initial model from init_seed + j."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for j in range(count):
+        N = int(rng.choice([3, 4]))
+        dims = tuple(int(round(math.exp(rng.uniform(math.log(50), math.log(5000))))) for _ in range(N))
+        nnz = int(round(math.exp(rng.uniform(math.log(1e3), math.log(1e6)))))
+        nnz = int(min(nnz, 0.5 * math.prod(dims)))
+        ranks = tuple(int(rng.integers(3, 11)) for _ in range(N))
+        jobs.append(Workload(f"c3_{j}", dims, ranks, nnz, "uniform", core_density=0.2, factor_density=0.4,
+                             noise=0.01, dtype="f32", reg="LF", lam=0.01, data_seed=seed * 1000 + j,
+                             init_seed=init_seed + j))
+    return jobs
+
+
+def make(w: Workload | str, device=None, **overrides):
+    """Returns (tensor, initial model state, planted model) for a workload.  With a torch
+    device the planted values are formed there (same numbers, faster)."""
     if isinstance(w, str):
         w = WORKLOADS[w]
     if overrides:
@@ -218,7 +262,10 @@ def make(w: Workload | str, **overrides):
     r_idx, r_model, r_noise = (np.random.default_rng(s) for s in ss.spawn(3))
     idx = sample_indices(r_idx, w.dims, w.nnz, w.dist, w.zipf_s)
     planted = planted_model(r_model, w.dims, w.ranks, w.core_density, w.factor_density, w.exact_zero_fraction)
-    x = planted_values(idx, planted, w.noise, r_noise)
+    if device is None:
+        x = planted_values(idx, planted, w.noise, r_noise)
+    else:
+        x = planted_values_on(device, idx, planted, w.noise, r_noise)
     np_dtype = np.float64 if w.dtype == "f64" else np.float32
     tensor = SparseTensor(tuple(w.dims), idx, x.astype(np_dtype))
     init = random_init(w.dims, w.ranks, w.init_seed, np_dtype)
