@@ -264,7 +264,8 @@ vest_status vest_loss_noalloc(const vest_index* ix, const vest_model* m, int32_t
                               void* resid, void* stream);
 
 /* Completion queries: B(alpha) (Eq. 7) for m query positions q_idx (device
- * int32 [order][m]) into out (device, model dtype, [m]). */
+ * int32 [order][m]) into out (device, model dtype, [m]).  A tuple with an index
+ * outside [0, I_n) reads nothing and gives NaN. */
 vest_status vest_reconstruct(const vest_model* m, const int32_t* q_idx, int64_t count, void* out,
                              void* stream);
 

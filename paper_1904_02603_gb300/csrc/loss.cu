@@ -256,6 +256,15 @@ template vest_status loss_impl<double>(const vest_index*, const vest_model*, int
 template <typename T>
 __global__ void reconstruct_kernel(DevModel<T> M, const int32_t* __restrict__ q, int64_t count, T* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    bool in_range = true;  // a tuple outside the tensor reads nothing and gives NaN
+    for (int n = 0; n < M.N; ++n) {
+      const int32_t v = q[(int64_t)n * count + i];
+      in_range = in_range && v >= 0 && (int64_t)v < M.I[n];
+    }
+    if (!in_range) {
+      out[i] = T(NAN);
+      continue;
+    }
     // B = sum over core elements, staged: fold the slowest mode first
     T acc = T(0);
     int64_t lin = 0;

@@ -346,6 +346,10 @@ def test_reconstruct_normalize_count_zeros():
     got = V.vest_reconstruct(mdl, torch.from_numpy(q).cuda()).cpu().numpy()
     ref = np.array([O.entry(om, q[:, i]) for i in range(500)])
     assert rel_err(got, ref) < 1e-12
+    bad = q[:, :4].copy()
+    bad[0, 0], bad[1, 1], bad[2, 2] = t.dims[0], -1, 1 << 30  # outside the tensor: NaN, nothing read
+    got_bad = V.vest_reconstruct(mdl, torch.from_numpy(bad).cuda()).cpu().numpy()
+    assert np.isnan(got_bad[:3]).all() and got_bad[3] == got[3]
     ix = V.vest_build_index(ten)
     sc = V.make_scratch(ix, mdl)
     z = V.vest_count_zeros(mdl, sc).cpu().numpy()

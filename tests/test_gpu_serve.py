@@ -1,0 +1,53 @@
+"""The request loop: every job's model and loss, and every query's values, are bitwise the same
+when served in the mix (continuous batching) as when run alone."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1904_02603_gb300 import batch as B
+from paper_1904_02603_gb300 import datagen
+from paper_1904_02603_gb300 import serve as S
+from paper_1904_02603_gb300 import vest as V
+
+pytestmark = pytest.mark.gpu
+
+
+def _specs():
+    shapes = [((60, 50, 40), (3, 4, 5), 3000), ((30, 20, 25, 15), (3, 3, 4, 2), 2500),
+              ((200, 90, 70), (10, 8, 6), 9000), ((500, 400, 300), (6, 7, 5), 20000)]
+    out = []
+    for j, (dims, ranks, nnz) in enumerate(shapes):
+        t, st = datagen.random_problem(4000 + j, dims, ranks, nnz, dtype=np.float32)
+        out.append((t, st, V.REG_LF, 0.02))
+    return out
+
+
+def _alone(spec, sweeps):
+    job = B.prepare([spec])[0]
+    B.sweeps(job, sweeps)
+    loss = V.vest_loss(job.index, job.model, job.reg, job.lam, job.scratch).cpu().numpy()
+    return job.model, loss
+
+
+def test_served_results_equal_alone_results():
+    specs = _specs()
+    reqs = S.make_trace(specs, rate=400.0, duration=0.08, seed=7)
+    assert any(r.kind == "query" for r in reqs) and any(r.kind == "job" for r in reqs)
+    server = S.Server(specs, slots=4, sweeps=3)
+    server.serve(reqs)
+    torch.cuda.synchronize()
+    alone = {}
+    for r in reqs:
+        if r.kind == "job":
+            mdl, loss = _alone(specs[r.spec], 3)
+            alone[r.rid] = mdl
+            np.testing.assert_array_equal(r.result, loss)
+            f1, c1, _, _ = server.models[r.rid][0].to_host()
+            f2, c2, _, _ = mdl.to_host()
+            assert all(np.array_equal(a, b) for a, b in zip(f1, f2)) and np.array_equal(c1, c2)
+    for r in reqs:
+        if r.kind == "query":
+            ref = V.vest_reconstruct(alone[r.target], torch.from_numpy(r.q_idx).cuda()).cpu().numpy()
+            np.testing.assert_array_equal(r.result, ref)
+    st = S.latency_stats(reqs)
+    assert st["requests"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0
