@@ -411,7 +411,7 @@ def main():
     w = datagen.WORKLOADS[args.workload]
     # every rank fits its own instance of the workload (weak scaling)
     ds, iseed = replica_seeds(w, rank)
-    t, st, _ = datagen.make(w, data_seed=ds, init_seed=iseed)
+    t, st, _ = datagen.make(w, device="cuda", data_seed=ds, init_seed=iseed)
     tdt = torch.float64 if w.dtype == "f64" else torch.float32
     reg = V.REG_LF if w.reg == "LF" else V.REG_L1
     ten = V.Tensor.from_host(t)
