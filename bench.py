@@ -37,6 +37,8 @@ from paper_1904_02603_gb300 import datagen  # noqa: E402
 METRIC = "CD-sweep nnz-updates/s"
 UNIT = "entry-mode updates/s"
 PRUNE_RATE = 0.01  # pr_1 = min(0.01 t, 0.1) at t = 1 (Algorithm 2)
+BATCH = "batch_256_jobs"
+SERVE = "serve_200rps"
 FP32_LANES_PER_SM = 128
 GB300_SMS = 152
 
@@ -47,11 +49,10 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="vest", choices=["vest", "reference"])
-    p.add_argument("--workload", default="c1", choices=sorted(datagen.WORKLOADS) + ["c3", "c4"],
-                   help="c3: the batched configuration (256 independent jobs, jobs/s); "
-                        "c4: the serving configuration (request trace, p50/p99 latency)")
-    p.add_argument("--duration", type=float, default=5.0, help="c4: seconds of Poisson arrivals")
-    p.add_argument("--streams", type=int, default=16, help="c3: streams the batched form replays its graphs on")
+    p.add_argument("--workload", default="zipf_1e5x3_1e7", choices=sorted(datagen.WORKLOADS) + [BATCH, SERVE],
+                   help=f"{BATCH}: 256 independent jobs (jobs/s); {SERVE}: a request trace (p50/p99 latency)")
+    p.add_argument("--duration", type=float, default=5.0, help=f"{SERVE}: seconds of Poisson arrivals")
+    p.add_argument("--streams", type=int, default=16, help="stream slots of the batched and served forms")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
@@ -103,6 +104,9 @@ def run_reference(args):
     """The oracle as it stands, timed on the host cores, on bounded samples of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload not in datagen.WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the one-tensor workloads only"}))
         return
     w = datagen.WORKLOADS[args.workload]
     t, st, _ = datagen.make(w)
@@ -228,8 +232,8 @@ def measured_peaks():
         return {}
 
 
-# ------------------------------------------------------------------ batched jobs (c3)
-C3_SWEEPS = 10
+# ------------------------------------------------------------------ batched jobs
+BATCH_SWEEPS = 10
 
 
 def main_batch(args):
@@ -272,10 +276,10 @@ def main_batch(args):
 
     steps, warm = max(1, args.steps), max(1, args.warmup)
     for _ in range(warm):
-        B.run_plain(plain, C3_SWEEPS)
-    plain_ms = timed(lambda: B.run_plain(plain, C3_SWEEPS), steps)
+        B.run_plain(plain, BATCH_SWEEPS)
+    plain_ms = timed(lambda: B.run_plain(plain, BATCH_SWEEPS), steps)
     captured0 = V.vest_launch_count()
-    run = B.BatchedRun(batched, C3_SWEEPS, n_streams=args.streams)
+    run = B.BatchedRun(batched, BATCH_SWEEPS, n_streams=args.streams)
     per_replay = V.vest_launch_count() - captured0  # kernels recorded in the graphs, launched by every replay
     for _ in range(warm):
         run.replay()
@@ -296,7 +300,7 @@ def main_batch(args):
         job = B.prepare([(t, st, reg, lam)])[0]
         ixe = V.vest_build_index(ten)
         job = B.Job(ten, job.model, ixe, job.scratch, reg, lam)
-        B.sweeps(job, C3_SWEEPS)
+        B.sweeps(job, BATCH_SWEEPS)
         loss = V.vest_loss(ixe, job.model, reg, lam, job.scratch).cpu()
         h2d += ih.numel() * ih.element_size() + vh.numel() * vh.element_size()
         d2h += loss.numel() * loss.element_size()
@@ -306,14 +310,14 @@ def main_batch(args):
         "metric": "jobs/s (batched factorisations, 10 sweeps each)", "value": len(ws) / (batched_ms / 1e3),
         "unit": "jobs/s", "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": batched_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "c3", "jobs": len(ws), "sweeps": C3_SWEEPS, "entries": entries,
+        "config": {"workload": BATCH, "jobs": len(ws), "sweeps": BATCH_SWEEPS, "entries": entries,
                    "streams": args.streams, "form": "one CUDA graph per job, replayed round-robin over streams",
                    "l2": "the batch's CSR arrays and factors (several GB) exceed the 129 MB L2",
                    "input_generation_s": gen_s},
         "plain": {"value": len(ws) / (plain_ms / 1e3), "unit": "jobs/s", "ms_per_step": plain_ms,
                   "form": "one job after another on one stream, each call launched as it goes"},
         "speedup_vs_plain": plain_ms / batched_ms,
-        "entry_mode_updates_per_s": sum(w.nnz * len(w.dims) for w in ws) * C3_SWEEPS / (batched_ms / 1e3),
+        "entry_mode_updates_per_s": sum(w.nnz * len(w.dims) for w in ws) * BATCH_SWEEPS / (batched_ms / 1e3),
         "e2e": {"value": 32 / e2e_s, "unit": "jobs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "includes": "32 jobs one by one: H2D of idx+val, index build, 10 sweeps, D2H of the loss"},
         "clocks": clk,
@@ -323,7 +327,7 @@ def main_batch(args):
     print(json.dumps(line), flush=True)
 
 
-# ------------------------------------------------------------------ serving (c4)
+# ------------------------------------------------------------------ serving
 def main_serve(args):
     """A Poisson trace at 200 requests/s, half factorisation jobs (drawn as in the batched
     configuration, 10 sweeps each) and half completion queries (1..1e5 tuples, log-uniform)
@@ -363,7 +367,7 @@ def main_serve(args):
         "metric": "p99 latency (continuous batching, 200 req/s)", "value": served["p99_ms"], "unit": "ms",
         "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": served["span_s"] * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "c4", "rate_per_s": 200, "duration_s": args.duration, "job_fraction": 0.5,
+        "config": {"workload": SERVE, "rate_per_s": 200, "duration_s": args.duration, "job_fraction": 0.5,
                    "slots": args.streams, "hbm_budget_gb": 150, "sweeps_per_job": 10,
                    "l2": "each job's inputs are copied in from host memory; the batch exceeds the 129 MB L2"},
         "served": served, "one_at_a_time": base,
@@ -382,10 +386,10 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.workload == "c3":
+    if args.workload == BATCH:
         main_batch(args)
         return
-    if args.workload == "c4":
+    if args.workload == SERVE:
         main_serve(args)
         return
     import torch

@@ -210,22 +210,23 @@ class Workload:
     init_seed: int = 2000
 
 
-# The configurations the library is measured and checked on.  c0..c2 carry the
-# paper's workload shapes (synthetic stand-ins for Table 2); the *_small ones keep
-# the same structure at sizes the FP64 oracle finishes in seconds.
+# The workloads the library is measured and checked on, named by their index
+# distribution, mode sizes and entry count: synthetic stand-ins for the paper's
+# workload shapes (Table 2); the small ones keep the same structure at sizes the
+# FP64 oracle finishes in seconds.
 WORKLOADS = {
-    "c0": Workload("c0", (100, 100, 100), (5, 5, 5), 10_000, "uniform", exact_zero_fraction=0.5,
+    "uniform_100x3_1e4": Workload("uniform_100x3_1e4", (100, 100, 100), (5, 5, 5), 10_000, "uniform", exact_zero_fraction=0.5,
                    noise=0.01, dtype="f64", reg="LF", lam=0.01, data_seed=1000, init_seed=2000),
-    "c1": Workload("c1", (100_000,) * 3, (10, 10, 10), 10_000_000, "zipf", 1.2, core_density=0.1,
+    "zipf_1e5x3_1e7": Workload("zipf_1e5x3_1e7", (100_000,) * 3, (10, 10, 10), 10_000_000, "zipf", 1.2, core_density=0.1,
                    factor_density=0.3, noise=0.01, dtype="f32", reg="LF", lam=0.01, data_seed=1001,
                    init_seed=2001),
-    "c2": Workload("c2", (10_000,) * 4, (8, 8, 8, 8), 50_000_000, "uniform", core_density=0.05,
+    "uniform_1e4x4_5e7": Workload("uniform_1e4x4_5e7", (10_000,) * 4, (8, 8, 8, 8), 50_000_000, "uniform", core_density=0.05,
                    factor_density=0.4, noise=0.05, dtype="f32", reg="L1", lam=0.1, data_seed=1002,
                    init_seed=2002),
-    "c1_small": Workload("c1_small", (2000,) * 3, (10, 10, 10), 40_000, "zipf", 1.2, core_density=0.1,
+    "zipf_2000x3_4e4": Workload("zipf_2000x3_4e4", (2000,) * 3, (10, 10, 10), 40_000, "zipf", 1.2, core_density=0.1,
                          factor_density=0.3, noise=0.01, dtype="f32", reg="LF", lam=0.01, data_seed=1011,
                          init_seed=2011),
-    "c2_small": Workload("c2_small", (300,) * 4, (8, 8, 8, 8), 20_000, "uniform", core_density=0.05,
+    "uniform_300x4_2e4": Workload("uniform_300x4_2e4", (300,) * 4, (8, 8, 8, 8), 20_000, "uniform", core_density=0.05,
                          factor_density=0.4, noise=0.05, dtype="f32", reg="L1", lam=0.1, data_seed=1012,
                          init_seed=2012),
 }
@@ -245,7 +246,7 @@ def batch_workloads(count: int = 256, seed: int = 1003, init_seed: int = 2003) -
         nnz = int(round(math.exp(rng.uniform(math.log(1e3), math.log(1e6)))))
         nnz = int(min(nnz, 0.5 * math.prod(dims)))
         ranks = tuple(int(rng.integers(3, 11)) for _ in range(N))
-        jobs.append(Workload(f"c3_{j}", dims, ranks, nnz, "uniform", core_density=0.2, factor_density=0.4,
+        jobs.append(Workload(f"batch_job_{j}", dims, ranks, nnz, "uniform", core_density=0.2, factor_density=0.4,
                              noise=0.01, dtype="f32", reg="LF", lam=0.01, data_seed=seed * 1000 + j,
                              init_seed=init_seed + j))
     return jobs

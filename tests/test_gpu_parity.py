@@ -170,9 +170,9 @@ def test_prune_threshold_mode():
 
 
 # ---------------------------------------------------------------- a9: auto-search, config-0 workload
-def test_c0_manual_pruning_run_f64():
+def test_manual_pruning_run_f64_uniform_100x3():
     """The 100^3 / 10^4-entry FP64 workload: 10 iterations, 20% of the remaining pruned each step."""
-    t, st, _ = datagen.make("c0")
+    t, st, _ = datagen.make("uniform_100x3_1e4")
     ten, mdl = device_pair(t, st)
     ix = V.vest_build_index(ten)
     sc = V.make_scratch(ix, mdl, autosearch=True)
@@ -206,7 +206,7 @@ def test_autosearch_auto_mode_f64():
 # ---------------------------------------------------------------- FP32 path vs FP64 oracle
 def test_fp32_objective_within_1e4_on_zipf_workload():
     """FP32 storage and products, FP64 row finishing: objective within 1e-4 of the FP64 oracle."""
-    t, st, _ = datagen.make("c1_small")
+    t, st, _ = datagen.make("zipf_2000x3_4e4")
     ten, mdl = device_pair(t, st, torch.float32)
     ix = V.vest_build_index(ten)
     sc = V.make_scratch(ix, mdl)
@@ -273,7 +273,7 @@ def test_iteration_without_responsibility_matches_separate_calls():
 
 def test_iteration_fp32_objective_within_1e4_on_zipf_workload():
     """The residual kept by the core sweep (FP32, updated block by block) gives the loss within 1e-4."""
-    t, st, _ = datagen.make("c1_small")
+    t, st, _ = datagen.make("zipf_2000x3_4e4")
     ten, mdl = device_pair(t, st, torch.float32)
     ix = V.vest_build_index(ten)
     sc = V.make_scratch(ix, mdl)

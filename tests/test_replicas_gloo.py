@@ -22,7 +22,7 @@ def _rank_main(rank: int, world: int, port: int, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        w = datagen.WORKLOADS["c0"]
+        w = datagen.WORKLOADS["uniform_100x3_1e4"]
         ds, iseed = bench.replica_seeds(w, rank)
         t, _, _ = datagen.make(w, data_seed=ds, init_seed=iseed)
         mine = 10.0 + 5.0 * rank  # each rank's own elapsed time
