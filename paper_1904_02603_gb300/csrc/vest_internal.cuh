@@ -203,17 +203,4 @@ vest_status reconstruct_impl(const vest_model* m, const int32_t* q_idx, int64_t 
 vest_status build_index_impl(const vest_tensor* t, void* ws, size_t ws_bytes, vest_index* ix, cudaStream_t s);
 size_t index_workspace_bytes(const vest_tensor* t);
 
-// ------------------------------------------------------------------ device helpers
-// Largest k in [0, n] with a[k] <= x (a sorted ascending, a[0] <= x).
-template <typename I>
-__device__ __forceinline__ int64_t upper_bound_m1(const I* a, int64_t n, int64_t x) {
-  int64_t lo = 0, hi = n;  // invariant: a[lo] <= x, answer in [lo, hi]
-  while (lo < hi) {
-    int64_t mid = (lo + hi + 1) >> 1;
-    if ((int64_t)a[mid] <= x) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 }  // namespace vest
