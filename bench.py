@@ -53,6 +53,9 @@ def parse():
                    help=f"{BATCH}: 256 independent jobs (jobs/s); {SERVE}: a request trace (p50/p99 latency)")
     p.add_argument("--duration", type=float, default=5.0, help=f"{SERVE}: seconds of Poisson arrivals")
     p.add_argument("--streams", type=int, default=16, help="stream slots of the batched and served forms")
+    p.add_argument("--autosearch", type=int, default=0,
+                   help="after the timed steps, run vest_autosearch (Algorithm 2, VeST_auto) for up to this many "
+                        "iterations from the initial model and report it")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
@@ -485,6 +488,23 @@ def main():
     value = whole_job_rate(world, units_per_step, args.steps, elapsed_ms)
     final_loss = loss.cpu().numpy().tolist()
 
+    # Algorithm 2 end to end (VeST_auto) from the initial model, after the timed region
+    auto = None
+    if args.autosearch > 0:
+        am = V.Model.from_host(st)
+        asc = V.make_scratch(ix, am, autosearch=True)
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        rep = V.vest_autosearch(ix, am, V.params(reg=reg, lam=w.lam, max_iter=args.autosearch), asc)
+        torch.cuda.synchronize()
+        ta = time.perf_counter() - ta
+        auto = {"iters": rep["iters"], "stop_iter": rep["stop_iter"], "final_sparsity": rep["final_sparsity"],
+                "re": [float(x) for x in rep["re"]], "pr": [float(x) for x in rep["pr"]],
+                "sparsity": [float(x) for x in rep["sparsity"]], "seconds": ta,
+                "ms_per_iteration": 1e3 * ta / max(rep["iters"], 1),
+                "mode": "VeST_auto: pr_t = min(0.01 t, 0.1), elbow threshold 0.05, count_mode total, normalised"}
+        del am, asc
+
     # per-operation breakdown through the separate entry points (after the timed region, on a copy)
     sep_model = mdl.clone()
     sep_evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
@@ -571,6 +591,7 @@ def main():
                                               % PRUNE_RATE}),
         "op_ms": op_ms,
         "separate_calls_ms": sep_ms,
+        "autosearch": auto,
         "sweep_only": {"value": world * units_per_step / (op_ms["sweep_factors"] / 1e3), "unit": UNIT},
         "final_loss": {"sq_err": final_loss[0], "objective": final_loss[3], "re": final_loss[4]},
         "roofline": roofline,
