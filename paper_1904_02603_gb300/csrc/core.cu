@@ -16,10 +16,13 @@
 //     merge expands Z into each packed M_b in FP64;
 //   - then per block in order: one pass over the mode-0 CSR applies the
 //     previous block's Delta to r and forms g_k = sum_alpha r_alpha P_alpha(k)
-//     (per piece h(q) = sum r w(q), g += a0 (x) h); one thread block performs
-//     the b updates in order with sum_alpha r P(k) = g_k - sum_{l<k} Delta_l M_lk.
+//     (per row segment h(q) = sum r w(q), g += a0 (x) h); one warp performs the
+//     b updates in order with sum_alpha r P(k) = g_k - sum_{l<k} Delta_l M_lk;
+//   - optionally a last light pass applies the last block's Delta, so r is the
+//     residual of the swept model (loss and responsibility then reuse it).
 // The core responsibility needs g and diag(M) of every element for a fixed r:
-// one stats pass per group of suffixes.
+// one stats pass per group of suffixes forms both, or g alone right after a core
+// sweep with the same factors, whose block Grams hold diag(M).
 // Sums: per piece in the storage type; across pieces and tasks FP32 with Kahan
 // compensation (or FP64); across thread blocks FP64 in a fixed order.
 #include <algorithm>
