@@ -39,6 +39,8 @@ UNIT = "entry-mode updates/s"
 PRUNE_RATE = 0.01  # pr_1 = min(0.01 t, 0.1) at t = 1 (Algorithm 2)
 BATCH = "batch_256_jobs"
 SERVE = "serve_200rps"
+SCALABILITY = "scalability"
+SPARSITY = "sparsity_curve"
 FP32_LANES_PER_SM = 128
 GB300_SMS = 152
 
@@ -49,8 +51,10 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="vest", choices=["vest", "reference"])
-    p.add_argument("--workload", default="zipf_1e5x3_1e7", choices=sorted(datagen.WORKLOADS) + [BATCH, SERVE],
-                   help=f"{BATCH}: 256 independent jobs (jobs/s); {SERVE}: a request trace (p50/p99 latency)")
+    p.add_argument("--workload", default="zipf_1e5x3_1e7", choices=sorted(datagen.WORKLOADS) + [BATCH, SERVE, SCALABILITY, SPARSITY],
+                   help=f"{BATCH}: 256 independent jobs (jobs/s); {SERVE}: a request trace (p50/p99 latency); "
+                        f"{SCALABILITY}: iteration time against order, mode size and entry count; "
+                        f"{SPARSITY}: training and held-out error against the target sparsity")
     p.add_argument("--duration", type=float, default=5.0, help=f"{SERVE}: seconds of Poisson arrivals")
     p.add_argument("--streams", type=int, default=16, help="stream slots of the batched and served forms")
     p.add_argument("--autosearch", type=int, default=0,
@@ -383,6 +387,177 @@ def main_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ scalability series
+def loglog_slope(xs, ys) -> float:
+    lx, ly = np.log(np.asarray(xs, np.float64)), np.log(np.asarray(ys, np.float64))
+    return float(np.polyfit(lx, ly, 1)[0]) if len(xs) > 1 else float("nan")
+
+
+def main_scalability(args):
+    """The data-scalability series of Section 4.5 on one GPU: one Algorithm 2 iteration (factor
+    sweep, core sweep, loss, responsibility, prune at pr = 0.01) timed at every point of three
+    series (order 3..10; mode size 1e3..1e8 with |Omega| = I; |Omega| 1e3..1e7), ranks 3, values
+    U(0,1), FP32.  value = entry-mode updates/s at the largest point (I = |Omega| = 1e8)."""
+    import torch
+
+    from paper_1904_02603_gb300 import build as Bd
+    from paper_1904_02603_gb300 import vest as V
+    if int(os.environ.get("RANK", "0")) != 0:
+        return  # the series runs on one GPU
+    torch.cuda.set_device(0)
+    Bd.build()
+    V.load()
+    stream = torch.cuda.current_stream()
+    steps, warm = max(1, min(args.steps, 5)), max(1, min(args.warmup, 3))
+    lam = 0.01
+    pts, launches, cpu_pts, cpu_total = [], 0, [], 0.0
+    clocks = ClockSampler(gpu_index_for_smi(0))
+    for k, (series, order, dim, nnz) in enumerate(datagen.scalability_points()):
+        t, st = datagen.uniform_tensor(order, dim, nnz, seed=3000 + k)
+        ten = V.Tensor.from_host(t)
+        mdl = V.Model.from_host(st)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ix = V.vest_build_index(ten)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        index_ms = e0.elapsed_time(e1)
+        sc = V.make_scratch(ix, mdl)
+        for _ in range(warm):
+            V.vest_iteration(ix, mdl, V.REG_LF, lam, PRUNE_RATE, sc)
+        torch.cuda.synchronize()
+        l0 = V.vest_launch_count()
+        e0.record(stream)
+        for _ in range(steps):
+            loss, _, _, _ = V.vest_iteration(ix, mdl, V.REG_LF, lam, PRUNE_RATE, sc)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        n_launch = V.vest_launch_count() - l0
+        launches += n_launch
+        ms = e0.elapsed_time(e2) / steps
+        re = float(loss.cpu().numpy()[4])
+        pts.append({"series": series, "order": order, "dim": dim, "nnz": nnz, "ms_per_iteration": ms,
+                    "index_build_ms": index_ms, "updates_per_s": order * nnz / (ms / 1e3),
+                    "launches_per_iteration": n_launch // steps, "re_after": re})
+        del ix, sc, mdl, ten
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    # the oracle on the order series, cheapest points first, within the CPU time budget
+    if not args.no_cpu_baseline:
+        for k, (series, order, dim, nnz) in enumerate(datagen.scalability_points()):
+            if series != "order" or cpu_total * 4 > args.cpu_seconds:
+                continue
+            t, st = datagen.uniform_tensor(order, dim, nnz, seed=3000 + k)
+            dt, _ = oracle_step_time(t, st.astype(np.float64), nnz, 0, lam)
+            cpu_total += dt
+            cpu_pts.append({"order": order, "dim": dim, "nnz": nnz, "ms_per_iteration": dt * 1e3})
+    slopes = {}
+    for series, key in (("order", "order"), ("dims", "dim"), ("nnz", "nnz")):
+        s_pts = [p for p in pts if p["series"] == series]
+        top = s_pts[len(s_pts) // 2:]
+        slopes[series] = {"all": loglog_slope([p[key] for p in s_pts], [p["ms_per_iteration"] for p in s_pts]),
+                          "upper_half": loglog_slope([p[key] for p in top], [p["ms_per_iteration"] for p in top])}
+    big = max((p for p in pts if p["series"] == "dims"), key=lambda p: p["dim"])
+    line = {
+        "metric": METRIC, "value": big["updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warm,
+        "ms_per_step": big["ms_per_iteration"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": SCALABILITY, "ranks": datagen.SCALABILITY_RANK, "values": "U(0,1)",
+                   "index_dist": "uniform", "reg": "LF", "lambda": lam, "init": "U(0,1) dense",
+                   "step": "one iteration of Algorithm 2 (vest_iteration, pr=%g)" % PRUNE_RATE,
+                   "value_at": "order 3, I = |Omega| = 1e8",
+                   "l2": "points up to 1e5 entries fit in L2 (no flush: the series measures the iteration as run)"},
+        "series": pts,
+        "loglog_slope_ms": slopes,
+        "cpu_baseline": {"value": None, "unit": "ms per iteration", "cores": 1, "kind": "oracle",
+                         "sample": "one full oracle iteration at each order-series point within the CPU budget",
+                         "points": cpu_pts} if cpu_pts else None,
+        "clocks": clk, "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ sparsity against error
+SPARSITY_TARGETS = (0.0, 0.2, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 0.95, 0.99)
+
+
+def main_sparsity_curve(args):
+    """Section 4.4 on planted data: VeST_man at each target sparsity and VeST_auto (the elbow
+    rule), for L_F and L_1, fitted on 90 % of the observed entries; RE on the training entries
+    and Test RE on the held-out 10 %, both from vest_loss over the respective index.  The Value
+    Pruning baseline of Section 4.1 (the s = 0 fit, then the 60 % smallest-magnitude elements of
+    every segment removed, no refit) is scored the same way."""
+    import torch
+
+    from paper_1904_02603_gb300 import build as Bd
+    from paper_1904_02603_gb300 import vest as V
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(0)
+    Bd.build()
+    V.load()
+    w = datagen.SPARSITY_CURVE
+    t, st, planted = datagen.make(w, device="cuda")
+    train, test = datagen.split_entries(t, 0.1)
+    ix_tr = V.vest_build_index(V.Tensor.from_host(train))
+    ix_te = V.vest_build_index(V.Tensor.from_host(test))
+    truth_zeros = sum(int((f == 0).sum()) for f in planted.factors) + int((planted.core == 0).sum())
+    truth_sparsity = truth_zeros / (planted.core.size + sum(f.size for f in planted.factors))
+    max_iter = 256  # CD from the U(0,1) start needs a few hundred sweeps on this tensor
+    total_elems = planted.core.size + sum(f.size for f in planted.factors)
+    curves, launches, total_s = {}, 0, 0.0
+    clocks = ClockSampler(gpu_index_for_smi(0))
+    for reg_name, reg in (("LF", V.REG_LF), ("L1", V.REG_L1)):
+        rows = []
+        for target in list(SPARSITY_TARGETS) + [-1.0]:
+            mdl = V.Model.from_host(st)
+            sc = V.make_scratch(ix_tr, mdl, autosearch=True)
+            sc_te = V.make_scratch(ix_te, mdl)
+            torch.cuda.synchronize()
+            l0 = V.vest_launch_count()
+            t0 = time.perf_counter()
+            rep = V.vest_autosearch(ix_tr, mdl, V.params(reg=reg, lam=w.lam, target_sparsity=target,
+                                                         max_iter=max_iter), sc)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            launches += V.vest_launch_count() - l0
+            total_s += secs
+            tr = V.vest_loss(ix_tr, mdl, reg, w.lam, sc).cpu().numpy()
+            te = V.vest_loss(ix_te, mdl, reg, w.lam, sc_te).cpu().numpy()
+            rows.append({"target": None if target < 0 else target, "mode": "auto" if target < 0 else "man",
+                         "sparsity": rep["final_sparsity"], "re_train": float(tr[4]), "re_test": float(te[4]),
+                         "iters": rep["iters"], "stop_iter": rep["stop_iter"], "seconds": secs})
+            if target == 0.0:  # Value Pruning: the unpruned fit, then |value| keys at ratio 0.6
+                kf, kc = V.vest_value_keys(mdl)
+                V.vest_prune(mdl, kf, kc, 0.6, sc, count_mode=1)
+                zeros = int(V.vest_count_zeros(mdl, sc).sum().item())
+                tr = V.vest_loss(ix_tr, mdl, reg, w.lam, sc).cpu().numpy()
+                te = V.vest_loss(ix_te, mdl, reg, w.lam, sc_te).cpu().numpy()
+                rows.append({"target": 0.6, "mode": "value_pruning", "sparsity": zeros / total_elems,
+                             "re_train": float(tr[4]), "re_test": float(te[4]), "iters": rep["iters"],
+                             "stop_iter": 0, "seconds": 0.0})
+            del mdl, sc, sc_te
+        curves[reg_name] = rows
+    clk = clocks.stop()
+    n_runs = sum(1 for rows in curves.values() for r in rows if r["mode"] != "value_pruning")
+    auto = next(r for r in curves["LF"] if r["mode"] == "auto")
+    line = {
+        "metric": "Test RE of VeST_auto (L_F) on held-out entries", "value": auto["re_test"], "unit": "RE",
+        "n_gpus": 1, "steps": n_runs, "warmup": 0, "ms_per_step": 1e3 * total_s / n_runs,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
+        "config": {**workload_config(w), "workload": SPARSITY, "tensor": w.name, "test_fraction": 0.1,
+                   "max_iter": max_iter, "truth_sparsity": truth_sparsity,
+                   "schedule": "pr_t = min(0.01 t, 0.1) of all elements; VeST_man stops pruning at the target, "
+                               "VeST_auto at the elbow (threshold 0.05); value_pruning: the s = 0 fit with the 60 % "
+                               "smallest |element| of each segment pruned, no refit"},
+        "curves": curves,
+        "seconds_total": total_s,
+        "clocks": clk, "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
@@ -394,6 +569,12 @@ def main():
         return
     if args.workload == SERVE:
         main_serve(args)
+        return
+    if args.workload == SCALABILITY:
+        main_scalability(args)
+        return
+    if args.workload == SPARSITY:
+        main_sparsity_curve(args)
         return
     import torch
     import torch.distributed as dist

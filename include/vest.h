@@ -121,6 +121,8 @@ typedef struct {
   double fixed_pr;
   int32_t count_mode;     /* 0: k = floor(pr * #unpruned); 1: k = floor(pr * size) */
   int32_t normalize;      /* 1: final column normalisation (Algorithm 2, last loop) */
+  int32_t revive_on_stop; /* VeST_auto only, 1: when the elbow rule stops pruning, unprune
+                             the elements the last pruning step removed (Section 3.5) */
 } vest_params;
 
 typedef struct {
@@ -203,6 +205,15 @@ vest_status vest_prune(vest_model* m, double* const* delta_factor, const double*
                        int32_t count_mode, int32_t threshold_mode, double tau, int64_t* n_pruned,
                        void* scratch, size_t scratch_bytes, void* stream);
 
+/* ---- Value Pruning keys (Section 4.1, competitors: VeST_man with s = 0, then
+ * value pruning with ratio 0.6).  Writes |element| in FP64 for every element
+ * of every segment: key_factor[n] is device double[I_n * J_n] row-major like
+ * A^(n), key_core device double[prod J_n] like G.  Passing them to vest_prune
+ * with pr = 0.6 and count_mode = 1 prunes, in each segment, the 60 % of its
+ * elements with the smallest magnitude (ties by linear index).  Buffers are
+ * caller-owned; NULL outputs give VEST_ERR_INVALID.  Never synchronises. */
+vest_status vest_value_keys(const vest_model* m, double* const* key_factor, double* key_core, void* stream);
+
 /* ---- a9: normalisation (Algorithm 2, last loop): A^(n) = U^(n) B^(n) with
  * unit-norm columns, A^(n) <- U^(n), G <- G x_n B^(n); zero columns stay 0. */
 vest_status vest_normalize(vest_model* m, void* scratch, size_t scratch_bytes, void* stream);
@@ -217,10 +228,14 @@ vest_status vest_count_zeros(const vest_model* m, int64_t* out, void* scratch, s
  * pr_t = min(init_pr * t, max_pr) (t = 1, 2, ...) or fixed_pr.  VeST_man
  * stops pruning once the sparsity reaches target_sparsity; VeST_auto stops
  * the first time t >= 3 and (RE_t + RE_{t-2} - 2 RE_{t-1}) / pr_t > elbow_thresh.
- * Ends at max_iter or when RE has converged after pruning stopped; then
- * normalises if asked.  Synchronises `stream` once per iteration to read RE.
- * report: host memory.  scratch: at least vest_autosearch_scratch_bytes()
- * (vest_scratch_bytes() plus room for the Delta scores of every element). */
+ * With revive_on_stop (VeST_auto), the masks return to their state before
+ * the last pruning step when the elbow rule fires; the revived elements hold 0
+ * until the next sweep refits them.  Ends at max_iter or when RE has converged
+ * after pruning stopped; then normalises if asked.  Synchronises `stream` once
+ * per iteration to read RE.  report: host memory.  scratch: at least
+ * vest_autosearch_scratch_bytes() (vest_scratch_bytes() plus 8 bytes per model
+ * element for the Delta scores and, with revive_on_stop, 1 byte per element for
+ * the saved masks); a smaller buffer gives VEST_ERR_WORKSPACE. */
 size_t vest_autosearch_scratch_bytes(const vest_index* ix, const vest_model* m);
 vest_status vest_autosearch(const vest_index* ix, vest_model* m, const vest_params* p, vest_report* report,
                             void* scratch, size_t scratch_bytes, void* stream);

@@ -65,7 +65,8 @@ class _Params(C.Structure):
     _fields_ = [("reg", C.c_int32), ("lambda_", C.c_double), ("init_pr", C.c_double),
                 ("max_pr", C.c_double), ("elbow_thresh", C.c_double), ("target_sparsity", C.c_double),
                 ("conv_tol", C.c_double), ("max_iter", C.c_int32), ("fixed_pr_mode", C.c_int32),
-                ("fixed_pr", C.c_double), ("count_mode", C.c_int32), ("normalize", C.c_int32)]
+                ("fixed_pr", C.c_double), ("count_mode", C.c_int32), ("normalize", C.c_int32),
+                ("revive_on_stop", C.c_int32)]
 
 
 class _Report(C.Structure):
@@ -312,13 +313,14 @@ class Params:
     fixed_pr: float = 0.0
     count_mode: int = 1
     normalize: int = 1
+    revive_on_stop: int = 0
 
     def cstruct(self):
         p = _Params()
         p.reg, p.lambda_, p.init_pr, p.max_pr = self.reg, self.lam, self.init_pr, self.max_pr
         p.elbow_thresh, p.target_sparsity, p.conv_tol = self.elbow_thresh, self.target_sparsity, self.conv_tol
         p.max_iter, p.fixed_pr_mode, p.fixed_pr = self.max_iter, self.fixed_pr_mode, self.fixed_pr
-        p.count_mode, p.normalize = self.count_mode, self.normalize
+        p.count_mode, p.normalize, p.revive_on_stop = self.count_mode, self.normalize, self.revive_on_stop
         return p
 
 

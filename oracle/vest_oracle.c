@@ -470,7 +470,11 @@ double or_elbow_stat(double re_t, double re_t1, double re_t2, double pr_t) {
  *   - VeST_auto stops pruning, for good, the first time t >= 3 and
  *     (RE_t + RE_{t-2} - 2 RE_{t-1}) / pr_t exceeds the threshold;
  *   - the loop ends at max_iter, or once pruning has stopped and
- *     |RE_{t-1} - RE_t| <= conv_tol * RE_{t-1}. */
+ *     |RE_{t-1} - RE_t| <= conv_tol * RE_{t-1};
+ *   - revive_on_stop (VeST_auto only; the paper describes it and leaves it
+ *     out of its runs): when the elbow rule fires, the masks go back to what
+ *     they were before the last pruning step, so the elements that step
+ *     removed are unpruned; they hold 0 until the next sweep refits them. */
 int or_autosearch(const or_tensor* t, or_model* m, const or_params* p, or_report* rep) {
   if (!valid(t, m) || !p || !rep || p->max_iter < 1 || p->max_iter > 256) return OR_ERR_INVALID;
   memset(rep, 0, sizeof(*rep));
@@ -482,7 +486,14 @@ int or_autosearch(const or_tensor* t, or_model* m, const or_params* p, or_report
     df[n] = (double*)malloc((size_t)(m->I[n] * m->J[n]) * sizeof(double));
     if (!df[n]) rc = OR_ERR_NOMEM;
   }
-  int pruning = 1;
+  int pruning = 1, saved = 0;
+  const int revive = p->revive_on_stop && p->target_sparsity < 0.0;
+  uint8_t* keep[OR_MAX_ORDER + 1] = {0}; /* masks before the last pruning step */
+  for (int32_t n = 0; revive && n <= m->N && rc == OR_OK; ++n) {
+    const int64_t sz = n < m->N ? m->I[n] * m->J[n] : gs;
+    keep[n] = (uint8_t*)calloc((size_t)(sz > 0 ? sz : 1), 1);
+    if (!keep[n]) rc = OR_ERR_NOMEM;
+  }
   double out[5];
   for (int32_t it = 1; rc == OR_OK && it <= p->max_iter; ++it) {
     rc = or_sweep_factors(t, m, p->reg, p->lambda, -1);
@@ -503,7 +514,19 @@ int or_autosearch(const or_tensor* t, or_model* m, const or_params* p, or_report
       }
       if (!pruning) {
         rep->stop_iter = it;
+        if (revive && saved) {
+          for (int32_t n = 0; n <= m->N; ++n) {
+            uint8_t* mk = n < m->N ? m->Amask[n] : m->Gmask;
+            if (mk) memcpy(mk, keep[n], (size_t)(n < m->N ? m->I[n] * m->J[n] : gs));
+          }
+        }
       } else {
+        for (int32_t n = 0; revive && n <= m->N; ++n) {
+          const int64_t sz = n < m->N ? m->I[n] * m->J[n] : gs;
+          const uint8_t* mk = n < m->N ? m->Amask[n] : m->Gmask;
+          if (mk) memcpy(keep[n], mk, (size_t)sz); else memset(keep[n], 0, (size_t)(sz > 0 ? sz : 1));
+        }
+        saved = revive;
         rc = or_responsibility(t, m, df, dc, NULL, NULL);
         if (rc == OR_OK) rc = or_prune(m, df, dc, pr, p->count_mode, 0, 0.0, NULL);
         rep->pr_hist[h] = pr;
@@ -518,5 +541,6 @@ int or_autosearch(const or_tensor* t, or_model* m, const or_params* p, or_report
   rep->final_sparsity = or_sparsity(m);
   free(dc);
   for (int32_t n = 0; n < m->N; ++n) free(df[n]);
+  for (int32_t n = 0; n <= m->N; ++n) free(keep[n]);
   return rc;
 }

@@ -58,6 +58,8 @@ typedef struct {
   double fixed_pr;
   int32_t count_mode;     /* 0: k = floor(pr * #unpruned); 1: k = floor(pr * size) */
   int32_t normalize;      /* 1: final column normalisation */
+  int32_t revive_on_stop; /* VeST_auto only: when the elbow rule stops pruning, the elements
+                             pruned by the last pruning step are unpruned again (Section 3.5) */
 } or_params;
 
 typedef struct {

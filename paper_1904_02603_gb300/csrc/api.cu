@@ -363,6 +363,15 @@ vest_status vest_prune(vest_model* m, double* const* delta_factor, const double*
                        static_cast<char*>(scratch), p2, as_stream(stream));
 }
 
+vest_status vest_value_keys(const vest_model* m, double* const* key_factor, double* key_core, void* stream) {
+  VEST_TRY(check_model(m));
+  if (!key_factor || !key_core) return fail(VEST_ERR_INVALID, "key outputs are NULL");
+  for (int n = 0; n < m->order; ++n)
+    if (!key_factor[n]) return fail(VEST_ERR_INVALID, "key_factor entry is NULL");
+  if (m->dtype == VEST_F64) return value_keys_impl<double>(m, key_factor, key_core, as_stream(stream));
+  return value_keys_impl<float>(m, key_factor, key_core, as_stream(stream));
+}
+
 vest_status vest_normalize(vest_model* m, void* scratch, size_t scratch_bytes, void* stream) {
   VEST_TRY(check_model(m));
   if (!scratch || scratch_bytes < normalize_scratch_bytes()) return fail(VEST_ERR_WORKSPACE, "scratch too small");
@@ -391,7 +400,7 @@ size_t vest_autosearch_scratch_bytes(const vest_index* ix, const vest_model* m) 
   int64_t total_elems = 1;
   for (int n = 0; n < m->order; ++n) total_elems *= m->ranks[n];
   for (int n = 0; n < m->order; ++n) total_elems += m->dims[n] * m->ranks[n];
-  return plan_scratch(ix, m).total + align_up((size_t)total_elems * 8);
+  return plan_scratch(ix, m).total + align_up((size_t)total_elems * 8) + align_up((size_t)total_elems);
 }
 
 vest_status vest_autosearch(const vest_index* ix, vest_model* m, const vest_params* p, vest_report* rep, void* scratch,
@@ -413,8 +422,22 @@ vest_status vest_autosearch(const vest_index* ix, vest_model* m, const vest_para
   for (int n = 0; n < m->order; ++n) total_elems *= m->ranks[n];
   const int64_t gs = total_elems;
   for (int n = 0; n < m->order; ++n) total_elems += m->dims[n] * m->ranks[n];
-  const size_t need = plan.total + align_up((size_t)total_elems * 8);
-  if (scratch_bytes < need) return fail(VEST_ERR_WORKSPACE, "auto-search needs vest_scratch_bytes() + 8 bytes per model element");
+  const bool revive = p->revive_on_stop != 0 && p->target_sparsity < 0.0;
+  const size_t need = plan.total + align_up((size_t)total_elems * 8) + (revive ? align_up((size_t)total_elems) : 0);
+  if (scratch_bytes < need) return fail(VEST_ERR_WORKSPACE, "auto-search scratch smaller than vest_autosearch_scratch_bytes()");
+  // the masks before the latest pruning step (revive_on_stop), segment after segment
+  uint8_t* saved = reinterpret_cast<uint8_t*>(sc + plan.total + align_up((size_t)total_elems * 8));
+  auto copy_masks = [&](bool save) -> vest_status {
+    uint8_t* at = saved;
+    for (int n = 0; n <= m->order; ++n) {
+      const size_t sz = n < m->order ? (size_t)(m->dims[n] * m->ranks[n]) : (size_t)gs;
+      uint8_t* mk = n < m->order ? m->factor_mask[n] : m->core_mask;
+      VEST_CUDA(cudaMemcpyAsync(save ? at : mk, save ? mk : at, sz, cudaMemcpyDeviceToDevice, s));
+      at += sz;
+    }
+    return VEST_OK;
+  };
+  bool have_saved = false;
   double* dbase = reinterpret_cast<double*>(sc + plan.total);
   double* dfac[VEST_MAX_ORDER];
   double* dptr = dbase;
@@ -434,7 +457,6 @@ vest_status vest_autosearch(const vest_index* ix, vest_model* m, const vest_para
     *out_sp = (double)z / total_size;
     return VEST_OK;
   };
-  (void)gs;
   bool pruning = true;
   for (int it = 1; it <= p->max_iter; ++it) {
     // the sweeps leave the residual of the swept model in the scratch: the loss and, when
@@ -460,7 +482,10 @@ vest_status vest_autosearch(const vest_index* ix, vest_model* m, const vest_para
       }
       if (!pruning) {
         rep->stop_iter = it;
+        if (revive && have_saved) VEST_TRY(copy_masks(false));
       } else {
+        if (revive) VEST_TRY(copy_masks(true));
+        have_saved = revive;
         VEST_TRY(iteration_prune(ix, m, loss, pr, p->count_mode, dfac, dcore, nullptr, sc, plan, s));
         rep->pr_hist[h] = pr;
       }

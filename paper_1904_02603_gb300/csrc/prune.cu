@@ -244,6 +244,28 @@ vest_status prune_impl(const vest_model* m, double* const* delta_factor, const d
   return VEST_OK;
 }
 
+// |value| in FP64 as the pruning key of every element: the Value Pruning baseline of the
+// evaluation (Section 4.1, competitors) selects through the same (key, index) order as
+// the responsibility prune.
+template <typename T>
+__global__ void value_keys_kernel(const T* __restrict__ v, int64_t size, double* __restrict__ key) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < size; e += (int64_t)gridDim.x * blockDim.x)
+    key[e] = fabs((double)v[e]);
+}
+
+template <typename T>
+vest_status value_keys_impl(const vest_model* m, double* const* key_factor, double* key_core, cudaStream_t s) {
+  const DevModel<T> M = dev_model<T>(m);
+  for (int seg = 0; seg <= M.N; ++seg) {
+    const bool core = seg == M.N;
+    const int64_t size = core ? M.gsize : M.I[seg] * M.J[seg];
+    const int grid = std::max(1, std::min<int>((int)ceil_div(size, 256), num_sms() * 4));
+    value_keys_kernel<T><<<grid, 256, 0, s>>>(core ? M.G : M.A[seg], size, core ? key_core : key_factor[seg]);
+    VEST_LAUNCH("value_keys");
+  }
+  return VEST_OK;
+}
+
 size_t prune_scratch_bytes(int64_t maxseg, size_t* keys_bytes, size_t* vals_bytes, size_t* tmp_bytes) {
   (void)maxseg;
   *keys_bytes = 0;
@@ -252,6 +274,8 @@ size_t prune_scratch_bytes(int64_t maxseg, size_t* keys_bytes, size_t* vals_byte
   return *keys_bytes + *vals_bytes + *tmp_bytes;
 }
 
+template vest_status value_keys_impl<float>(const vest_model*, double* const*, double*, cudaStream_t);
+template vest_status value_keys_impl<double>(const vest_model*, double* const*, double*, cudaStream_t);
 template vest_status prune_impl<float>(const vest_model*, double* const*, const double*, double, int, int, double,
                                        int64_t*, char*, const ScratchPlan&, cudaStream_t);
 template vest_status prune_impl<double>(const vest_model*, double* const*, const double*, double, int, int, double,

@@ -194,6 +194,8 @@ vest_status prune_impl(const vest_model* m, double* const* delta_factor, const d
                        int count_mode, int threshold_mode, double tau, int64_t* n_pruned, char* scratch,
                        const ScratchPlan& plan, cudaStream_t s);
 template <typename T>
+vest_status value_keys_impl(const vest_model* m, double* const* key_factor, double* key_core, cudaStream_t s);
+template <typename T>
 vest_status normalize_impl(const vest_model* m, char* scratch, cudaStream_t s);
 template <typename T>
 vest_status count_zeros_impl(const vest_model* m, int64_t* out, char* scratch, cudaStream_t s);

@@ -282,3 +282,61 @@ def random_problem(seed: int, dims, ranks, nnz: int, dtype=np.float64, dist: str
     x = planted_values(idx, planted, 0.01, rng)
     init = random_init(dims, ranks, seed + 7919, dtype)
     return SparseTensor(tuple(int(d) for d in dims), idx, x.astype(dtype)), init
+
+
+# ---------------------------------------------------------------- scalability series (Section 4.5)
+# The paper's data-scalability study: every mode the same size I, every rank 3, entry values
+# uniform in [0, 1]; three series, each varying one quantity.
+SCALABILITY_RANK = 3
+
+
+def scalability_points() -> list:
+    """(series, order N, mode size I, |Omega|) of the three series: the order 3..10 at
+    I = |Omega| = 1e3; the mode size 1e3..1e8 at N = 3 with |Omega| = I; |Omega| 1e3..1e7 at
+    N = 3, I = 1e3."""
+    pts = [("order", n, 1000, 1000) for n in range(3, 11)]
+    pts += [("dims", 3, 10 ** e, 10 ** e) for e in range(3, 9)]
+    pts += [("nnz", 3, 1000, 10 ** e) for e in range(3, 8)]
+    return pts
+
+
+def uniform_tensor(order: int, dim: int, nnz: int, seed: int, dtype=np.float32):
+    """A `order`-way tensor with every mode of size `dim`, `nnz` observed positions drawn uniformly
+    and values U(0,1), with a U(0,1) initial model of rank 3 per mode.  Positions are distinct
+    where the tensor has fewer than 2^62 cells; above that they are independent draws (the
+    expected number of repeated positions, nnz^2 / (2 dim^order), is below 1e-7 at every
+    point of the series)."""
+    ss = np.random.SeedSequence(seed)
+    r_idx, r_val, r_init = (np.random.default_rng(s) for s in ss.spawn(3))
+    dims = (int(dim),) * order
+    if math.prod(dims) < 2 ** 62:
+        idx = sample_indices(r_idx, dims, nnz, "uniform")
+    else:
+        idx = r_idx.integers(0, dim, size=(order, nnz), dtype=np.int32)
+    val = r_val.random(nnz, dtype=np.float64).astype(dtype)
+    ranks = (SCALABILITY_RANK,) * order
+    factors = [r_init.random((dim, SCALABILITY_RANK), dtype=np.float32).astype(dtype) for _ in range(order)]
+    core = r_init.random(SCALABILITY_RANK ** order, dtype=np.float32).astype(dtype)
+    assert tuple(f.shape[1] for f in factors) == ranks
+    return SparseTensor(dims, idx, val), ModelState(factors, core)
+
+
+# ---------------------------------------------------------------- held-out split (Section 4.3)
+def split_entries(t: SparseTensor, test_fraction: float = 0.1, seed: int = 1005):
+    """The observed entries split at random into a training tensor (1 - test_fraction of them)
+    and a held-out tensor (the rest), each keeping the input's order of entries."""
+    rng = np.random.default_rng(seed)
+    n_test = int(round(test_fraction * t.nnz))
+    test = np.zeros(t.nnz, bool)
+    test[rng.permutation(t.nnz)[:n_test]] = True
+    train_t = SparseTensor(t.dims, np.ascontiguousarray(t.idx[:, ~test]), np.ascontiguousarray(t.val[~test]))
+    test_t = SparseTensor(t.dims, np.ascontiguousarray(t.idx[:, test]), np.ascontiguousarray(t.val[test]))
+    return train_t, test_t
+
+
+# A planted sparse Tucker tensor for the sparsity-versus-error curves (Section 4.4): the truth
+# has 90 % of its core and 70 % of its factor elements at zero (overall sparsity 0.71), so the
+# reconstruction error of a fit should stay flat as the target sparsity grows to about there.
+SPARSITY_CURVE = Workload("planted_1000x3_1e6", (1000, 1000, 1000), (10, 10, 10), 1_000_000, "uniform",
+                          core_density=0.1, factor_density=0.3, noise=0.01, dtype="f32", reg="LF", lam=0.01,
+                          data_seed=1006, init_seed=2006)

@@ -51,7 +51,7 @@ class vest_params(C.Structure):
     _fields_ = [("reg", C.c_int32), ("lambda_", C.c_double), ("init_pr", C.c_double), ("max_pr", C.c_double),
                 ("elbow_thresh", C.c_double), ("target_sparsity", C.c_double), ("conv_tol", C.c_double),
                 ("max_iter", C.c_int32), ("fixed_pr_mode", C.c_int32), ("fixed_pr", C.c_double),
-                ("count_mode", C.c_int32), ("normalize", C.c_int32)]
+                ("count_mode", C.c_int32), ("normalize", C.c_int32), ("revive_on_stop", C.c_int32)]
 
 
 class vest_report(C.Structure):
@@ -82,6 +82,7 @@ _SIGS = {
                              C.c_size_t, _P]),
     "vest_normalize": (C.c_int, [C.POINTER(vest_model), _P, C.c_size_t, _P]),
     "vest_count_zeros": (C.c_int, [C.POINTER(vest_model), _P, _P, C.c_size_t, _P]),
+    "vest_value_keys": (C.c_int, [C.POINTER(vest_model), _P, _P, _P]),
     "vest_autosearch_scratch_bytes": (C.c_size_t, [_P, C.POINTER(vest_model)]),
     "vest_autosearch": (C.c_int, [_P, C.POINTER(vest_model), C.POINTER(vest_params), C.POINTER(vest_report), _P,
                                   C.c_size_t, _P]),
@@ -349,6 +350,15 @@ def vest_responsibility(ix: Index, m: Model, scratch: torch.Tensor, with_resp: b
     return df, dc, rf, rc
 
 
+def vest_value_keys(m: Model, stream=None):
+    """Returns (|A^(n)| per mode, |G|) as device float64: the Value Pruning keys for vest_prune."""
+    kf = [torch.empty(f.shape, dtype=torch.float64, device="cuda") for f in m.factors]
+    kc = torch.empty(m.core.shape, dtype=torch.float64, device="cuda")
+    kfa = _ptr_array(kf)
+    _call("vest_value_keys", C.byref(m.cstruct()), C.cast(kfa, C.c_void_p), _dptr(kc), _stream(stream))
+    return kf, kc
+
+
 def vest_prune(m: Model, delta_factor, delta_core, pr: float, scratch: torch.Tensor, count_mode: int = 0,
                threshold_mode: int = 0, tau: float = 0.0, stream=None) -> torch.Tensor:
     """Returns the device int64[order+1] pruned counts."""
@@ -399,11 +409,13 @@ def vest_reconstruct(m: Model, q_idx: torch.Tensor, stream=None) -> torch.Tensor
 
 
 def params(reg=REG_LF, lam=0.01, init_pr=0.01, max_pr=0.1, elbow_thresh=0.05, target_sparsity=-1.0,
-           conv_tol=1e-6, max_iter=50, fixed_pr_mode=0, fixed_pr=0.0, count_mode=1, normalize=1) -> vest_params:
+           conv_tol=1e-6, max_iter=50, fixed_pr_mode=0, fixed_pr=0.0, count_mode=1, normalize=1,
+           revive_on_stop=0) -> vest_params:
     p = vest_params()
     p.reg, p.lambda_, p.init_pr, p.max_pr = reg, lam, init_pr, max_pr
     p.elbow_thresh, p.target_sparsity, p.conv_tol, p.max_iter = elbow_thresh, target_sparsity, conv_tol, max_iter
     p.fixed_pr_mode, p.fixed_pr, p.count_mode, p.normalize = fixed_pr_mode, fixed_pr, count_mode, normalize
+    p.revive_on_stop = revive_on_stop
     return p
 
 

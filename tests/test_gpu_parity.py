@@ -203,6 +203,47 @@ def test_autosearch_auto_mode_f64():
     assert model_err(mdl, om) < TOL64
 
 
+def test_autosearch_revive_on_stop_f64():
+    """VeST_auto with revive_on_stop against the oracle: the elbow fires at iteration 4 on this
+    problem, and the masks go back to those before the prune of iteration 3."""
+    t, st = datagen.random_problem(42, (30, 25, 20), (3, 3, 3), 3000)
+    ten, mdl = device_pair(t, st)
+    ix = V.vest_build_index(ten)
+    sc = V.make_scratch(ix, mdl, autosearch=True)
+    kw = dict(lam=0.05, init_pr=0.05, max_pr=0.2, max_iter=12, conv_tol=1e-9, normalize=0, revive_on_stop=1)
+    rep = V.vest_autosearch(ix, mdl, V.params(reg=V.REG_LF, **kw), sc)
+    prob, om = oracle_pair(t, st)
+    orep = O.autosearch(prob, om, O.Params(reg=O.REG_LF, **kw))
+    assert rep["stop_iter"] == orep["stop_iter"] >= 3 and rep["iters"] == orep["iters"]
+    assert rel_err(rep["re"], orep["re"]) < TOL64
+    np.testing.assert_array_equal(rep["sparsity"], orep["sparsity"])
+    assert masks_equal(mdl, om)
+    assert model_err(mdl, om) < TOL64
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_value_pruning_keys_and_prune(dtype):
+    """Value Pruning: |element| keys bit-exact, then the 60 % smallest per segment pruned as the
+    oracle's prune does with the same keys."""
+    t, st = make_case("zipf_heavy")
+    st = with_masks(st, 0.1, 17)
+    ten, mdl = device_pair(t, st, dtype)
+    ix = V.vest_build_index(ten)
+    sc = V.make_scratch(ix, mdl)
+    V.vest_sweep_factors(ix, mdl, V.REG_LF, 0.05, -1, sc)
+    V.vest_sweep_core(ix, mdl, V.REG_LF, 0.05, sc)
+    om = oracle_from_device(mdl)
+    kf, kc = V.vest_value_keys(mdl)
+    for n in range(t.N):
+        np.testing.assert_array_equal(kf[n].cpu().numpy(), np.abs(om.A[n]))
+    np.testing.assert_array_equal(kc.cpu().numpy(), np.abs(om.G))
+    npr = V.vest_prune(mdl, kf, kc, 0.6, sc, count_mode=1)
+    onp = O.prune(om, [np.abs(a) for a in om.A], np.abs(om.G), 0.6, 1)
+    np.testing.assert_array_equal(npr.cpu().numpy(), onp)
+    assert masks_equal(mdl, om)
+    assert model_err(mdl, om) == 0.0
+
+
 # ---------------------------------------------------------------- FP32 path vs FP64 oracle
 def test_fp32_objective_within_1e4_on_zipf_workload():
     """FP32 storage and products, FP64 row finishing: objective within 1e-4 of the FP64 oracle."""

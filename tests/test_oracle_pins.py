@@ -387,6 +387,31 @@ def test_autosearch_auto_mode_stops_at_first_elbow(oracle_lib):
     assert rep["stop_iter"] == (fire or 0)
 
 
+def test_autosearch_revive_restores_the_masks_before_the_last_prune(oracle_lib):
+    """VeST_auto with revive_on_stop: when the elbow fires at iteration k, the masks go back to
+    those after iteration k-2 (before the prune of iteration k-1); the run up to k is unchanged."""
+    def run(revive, max_iter):
+        prob, model = small_problem(42, (30, 25, 20), (3, 3, 3), 3000)
+        p = O.Params(reg=O.REG_LF, lam=0.05, init_pr=0.05, max_pr=0.2, target_sparsity=-1.0, max_iter=max_iter,
+                     conv_tol=1e-9, normalize=0, revive_on_stop=revive)
+        return O.autosearch(prob, model, p), model
+
+    plain, m_plain = run(0, 30)
+    rev, m_rev = run(1, 30)
+    k = rev["stop_iter"]
+    assert k == plain["stop_iter"] and k >= 3
+    np.testing.assert_array_equal(rev["re"][:k], plain["re"][:k])
+    np.testing.assert_array_equal(rev["sparsity"][:k], plain["sparsity"][:k])
+    before, m_before = run(0, k - 2)  # stops right after the prune of iteration k-2
+    assert before["iters"] == k - 2
+    for a, b in zip(m_rev.Amask, m_before.Amask):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(m_rev.Gmask, m_before.Gmask)
+    assert any((a != b).any() for a, b in zip(m_plain.Amask + [m_plain.Gmask], m_before.Amask + [m_before.Gmask]))
+    # revived elements are refit by the next sweep: the value sparsity drops back to that of k-2
+    assert rev["sparsity"][k] == plain["sparsity"][k - 3] < plain["sparsity"][k]
+
+
 def test_planted_model_is_recovered(oracle_lib):
     # noiseless, fully observed, rank-matched: CD drives RE towards 0 (a sanity check,
     # not a pin: the problem is non-convex and some starts plateau for a long time)
