@@ -394,7 +394,7 @@ def loglog_slope(xs, ys) -> float:
 
 
 def main_scalability(args):
-    """The data-scalability series of Section 4.5 on one GPU: one Algorithm 2 iteration (factor
+    """The data-scalability series of Section 4.4 on one GPU: one Algorithm 2 iteration (factor
     sweep, core sweep, loss, responsibility, prune at pr = 0.01) timed at every point of three
     series (order 3..10; mode size 1e3..1e8 with |Omega| = I; |Omega| 1e3..1e7), ranks 3, values
     U(0,1), FP32.  value = entry-mode updates/s at the largest point (I = |Omega| = 1e8)."""
@@ -483,7 +483,7 @@ SPARSITY_TARGETS = (0.0, 0.2, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 0.95, 0.99)
 
 
 def main_sparsity_curve(args):
-    """Section 4.4 on planted data: VeST_man at each target sparsity and VeST_auto (the elbow
+    """Section 4.3 on planted data: VeST_man at each target sparsity and VeST_auto (the elbow
     rule), for L_F and L_1, fitted on 90 % of the observed entries; RE on the training entries
     and Test RE on the held-out 10 %, both from vest_loss over the respective index.  The Value
     Pruning baseline of Section 4.1 (the s = 0 fit, then the 60 % smallest-magnitude elements of

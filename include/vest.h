@@ -33,7 +33,7 @@
  *   - Model: factor A^(n) is I_n x J_n row-major; core G has prod_n J_n
  *     entries with linear index j_1 fastest (lin = j_1 + J_1 (j_2 + J_2 (...))),
  *     the mode-n matricisation convention of Section 2.1.  Masks are the
- *     marking table of Section 3.4: one byte per element, 1 = pruned (value 0,
+ *     marking table of Section 3.3: one byte per element, 1 = pruned (value 0,
  *     never updated again).  The tensor values, factors and core share one
  *     dtype.
  *   - Limits: 2 <= order <= VEST_MAX_ORDER, 1 <= J_n <= VEST_MAX_RANK,
@@ -107,7 +107,7 @@ typedef struct {
   const int32_t* nrows_nonempty; /* device scalar R_n */
 } vest_mode_view;
 
-/* Auto-search parameters (Algorithm 2, Section 3.4). */
+/* Auto-search parameters (Algorithm 2, Section 3.3). */
 typedef struct {
   int32_t reg;            /* vest_reg */
   double lambda;          /* > 0 */
@@ -122,7 +122,7 @@ typedef struct {
   int32_t count_mode;     /* 0: k = floor(pr * #unpruned); 1: k = floor(pr * size) */
   int32_t normalize;      /* 1: final column normalisation (Algorithm 2, last loop) */
   int32_t revive_on_stop; /* VeST_auto only, 1: when the elbow rule stops pruning, unprune
-                             the elements the last pruning step removed (Section 3.5) */
+                             the elements the last pruning step removed (Section 3.1) */
 } vest_params;
 
 typedef struct {
@@ -170,7 +170,7 @@ vest_status vest_sweep_factors(const vest_index* ix, vest_model* m, int32_t reg,
 
 /* ---- a5: core sweep (Lemma 2, Eq. 12 for L_F; Lemma 4, Eq. 14 for L_1).
  * Sequential CD over the unpruned core elements in linear order; results
- * equal, in exact arithmetic, one element at a time (Section 3.6). */
+ * equal, in exact arithmetic, one element at a time (Section 3.5). */
 vest_status vest_sweep_core(const vest_index* ix, vest_model* m, int32_t reg, double lambda,
                             void* scratch, size_t scratch_bytes, void* stream);
 
@@ -192,7 +192,7 @@ vest_status vest_responsibility(const vest_index* ix, const vest_model* m, doubl
                                 double* delta_core, double* const* resp_factor, double* resp_core,
                                 void* scratch, size_t scratch_bytes, void* stream);
 
-/* ---- a8: prune (Section 3.4; last step of Algorithm 3).  For each A^(n) and
+/* ---- a8: prune (Section 3.3; last step of Algorithm 3).  For each A^(n) and
  * for G separately, among unpruned elements select the k smallest Delta
  * (ties: smaller linear index first; -0 == +0), k = floor(pr * #unpruned)
  * (count_mode 0) or floor(pr * size) (count_mode 1), capped at #unpruned; or,
@@ -223,7 +223,7 @@ vest_status vest_normalize(vest_model* m, void* scratch, size_t scratch_bytes, v
 vest_status vest_count_zeros(const vest_model* m, int64_t* out, void* scratch, size_t scratch_bytes,
                              void* stream);
 
-/* ---- a9: auto-search (Algorithm 2, Section 3.4): iterations of factor sweep,
+/* ---- a9: auto-search (Algorithm 2, Section 3.3): iterations of factor sweep,
  * core sweep, RE, and, while should_prune(), responsibility + prune with
  * pr_t = min(init_pr * t, max_pr) (t = 1, 2, ...) or fixed_pr.  VeST_man
  * stops pruning once the sparsity reaches target_sparsity; VeST_auto stops

@@ -227,7 +227,7 @@ int or_sweep_factors(const or_tensor* t, or_model* m, int32_t reg, double lambda
 }
 
 /* Eq. 12 (L_F) / Eq. 14 (L_1), one core element at a time in linear order
- * (the core elements depend on each other, Section 3.6), pruned ones skipped.
+ * (the core elements depend on each other, Section 3.5), pruned ones skipped.
  * The sum over alpha of (X_alpha - sum_{gamma != beta} G_gamma P_alpha(gamma))
  * is evaluated as r_alpha + G_beta P_alpha(beta) with r = X - B kept current
  * after every update (the same bookkeeping Algorithm 3 uses with B(alpha));
@@ -364,7 +364,7 @@ static int cand_cmp(const void* pa, const void* pb) {
   return (a->index > b->index) - (a->index < b->index);
 }
 
-/* Section 3.4 pruning: per matrix (each A^(n), and G separately), sort the
+/* Section 3.3 pruning: per matrix (each A^(n), and G separately), sort the
  * unpruned elements by responsibility ascending and prune the smallest
  * k = floor(pr * #unpruned) (count_mode 0) or floor(pr * size) (count_mode 1,
  * the printed pr|G|), capped at #unpruned; a pruned element is set to zero

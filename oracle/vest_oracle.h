@@ -59,7 +59,7 @@ typedef struct {
   int32_t count_mode;     /* 0: k = floor(pr * #unpruned); 1: k = floor(pr * size) */
   int32_t normalize;      /* 1: final column normalisation */
   int32_t revive_on_stop; /* VeST_auto only: when the elbow rule stops pruning, the elements
-                             pruned by the last pruning step are unpruned again (Section 3.5) */
+                             pruned by the last pruning step are unpruned again (Section 3.1) */
 } or_params;
 
 typedef struct {
@@ -91,14 +91,14 @@ int or_sweep_core(const or_tensor* t, or_model* m, int32_t reg, double lambda);
 /* Definition 1-2, Eq. 3-6, Algorithm 3 (scores only) */
 int or_responsibility(const or_tensor* t, const or_model* m, double* const* delta_factor,
                       double* delta_core, double* const* resp_factor, double* resp_core);
-/* Pruning with the marking table (Section 3.4, Algorithm 3 last step) */
+/* Pruning with the marking table (Section 3.3, Algorithm 3 last step) */
 int or_prune(or_model* m, double* const* delta_factor, const double* delta_core, double pr,
              int32_t count_mode, int32_t threshold_mode, double tau, int64_t* n_pruned);
 /* Algorithm 2, final loop: unit-norm columns, core rescaled */
 int or_normalize(or_model* m);
 /* fraction of exactly-zero elements over |G| + sum_n I_n J_n */
 double or_sparsity(const or_model* m);
-/* VeST_auto stop statistic (Section 3.4): (RE_t + RE_{t-2} - 2 RE_{t-1}) / pr_t */
+/* VeST_auto stop statistic (Section 3.3): (RE_t + RE_{t-2} - 2 RE_{t-1}) / pr_t */
 double or_elbow_stat(double re_t, double re_t1, double re_t2, double pr_t);
 /* Algorithm 2 */
 int or_autosearch(const or_tensor* t, or_model* m, const or_params* p, or_report* rep);

@@ -2,7 +2,7 @@
 // responsibility (Eq. 5, Algorithm 3).
 //
 // The core elements are updated one at a time in linear order (j_1 fastest),
-// as the paper requires (Section 3.6).  On the GPU this is blocked
+// as the paper requires (Section 3.5).  On the GPU this is blocked
 // Gauss-Seidel, equal to the one-at-a-time sweep in exact arithmetic:
 //   - a block is b = J_0 * m consecutive core elements, (j_0, j_1) in
 //     J_0 x [q0, q0 + m) for one suffix s = (j_2, ..., j_{N-1});

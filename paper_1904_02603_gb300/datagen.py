@@ -284,7 +284,7 @@ def random_problem(seed: int, dims, ranks, nnz: int, dtype=np.float64, dist: str
     return SparseTensor(tuple(int(d) for d in dims), idx, x.astype(dtype)), init
 
 
-# ---------------------------------------------------------------- scalability series (Section 4.5)
+# ---------------------------------------------------------------- scalability series (Section 4.4)
 # The paper's data-scalability study: every mode the same size I, every rank 3, entry values
 # uniform in [0, 1]; three series, each varying one quantity.
 SCALABILITY_RANK = 3
@@ -321,7 +321,7 @@ def uniform_tensor(order: int, dim: int, nnz: int, seed: int, dtype=np.float32):
     return SparseTensor(dims, idx, val), ModelState(factors, core)
 
 
-# ---------------------------------------------------------------- held-out split (Section 4.3)
+# ---------------------------------------------------------------- held-out split (Section 4.2)
 def split_entries(t: SparseTensor, test_fraction: float = 0.1, seed: int = 1005):
     """The observed entries split at random into a training tensor (1 - test_fraction of them)
     and a held-out tensor (the rest), each keeping the input's order of entries."""
@@ -334,7 +334,7 @@ def split_entries(t: SparseTensor, test_fraction: float = 0.1, seed: int = 1005)
     return train_t, test_t
 
 
-# A planted sparse Tucker tensor for the sparsity-versus-error curves (Section 4.4): the truth
+# A planted sparse Tucker tensor for the sparsity-versus-error curves (Section 4.3): the truth
 # has 90 % of its core and 70 % of its factor elements at zero (overall sparsity 0.71), so the
 # reconstruction error of a fit should stay flat as the target sparsity grows to about there.
 SPARSITY_CURVE = Workload("planted_1000x3_1e6", (1000, 1000, 1000), (10, 10, 10), 1_000_000, "uniform",

@@ -1,4 +1,4 @@
-"""Order 10 with every rank 3, the top of the order series of the scalability study (Section 4.5).
+"""Order 10 with every rank 3, the top of the order series of the scalability study (Section 4.4).
 
 At this order the permuted core (3^10 elements, padded to 4 per mode-n fibre) no longer fits in
 shared memory, so the factor sweep and the loss read it from global memory, and the core
