@@ -123,6 +123,8 @@ typedef struct {
   int32_t normalize;      /* 1: final column normalisation (Algorithm 2, last loop) */
   int32_t revive_on_stop; /* VeST_auto only, 1: when the elbow rule stops pruning, unprune
                              the elements the last pruning step removed (Section 3.1) */
+  int32_t resume;         /* 1: continue the run recorded in the report passed in (a checkpoint:
+                             iters done, histories, stop_iter) on the model as it stands */
 } vest_params;
 
 typedef struct {
@@ -230,7 +232,12 @@ vest_status vest_count_zeros(const vest_model* m, int64_t* out, void* scratch, s
  * the first time t >= 3 and (RE_t + RE_{t-2} - 2 RE_{t-1}) / pr_t > elbow_thresh.
  * With revive_on_stop (VeST_auto), the masks return to their state before
  * the last pruning step when the elbow rule fires; the revived elements hold 0
- * until the next sweep refits them.  Ends at max_iter or when RE has converged
+ * until the next sweep refits them.  With resume, the loop continues from
+ * iteration report->iters + 1 with the report's histories (report->iters in
+ * [0, 256], else VEST_ERR_INVALID) and keeps pruning unless report->stop_iter
+ * is set: a run of K iterations with normalize = 0, resumed to max_iter from
+ * its model and report, gives bitwise the same model and report as one run to
+ * max_iter (a revive only restores prunes made after the resume).  Ends at max_iter or when RE has converged
  * after pruning stopped; then normalises if asked.  Synchronises `stream` once
  * per iteration to read RE.  report: host memory.  scratch: at least
  * vest_autosearch_scratch_bytes() (vest_scratch_bytes() plus 8 bytes per model

@@ -66,7 +66,7 @@ class _Params(C.Structure):
                 ("max_pr", C.c_double), ("elbow_thresh", C.c_double), ("target_sparsity", C.c_double),
                 ("conv_tol", C.c_double), ("max_iter", C.c_int32), ("fixed_pr_mode", C.c_int32),
                 ("fixed_pr", C.c_double), ("count_mode", C.c_int32), ("normalize", C.c_int32),
-                ("revive_on_stop", C.c_int32)]
+                ("revive_on_stop", C.c_int32), ("resume", C.c_int32)]
 
 
 class _Report(C.Structure):
@@ -314,6 +314,7 @@ class Params:
     count_mode: int = 1
     normalize: int = 1
     revive_on_stop: int = 0
+    resume: int = 0
 
     def cstruct(self):
         p = _Params()
@@ -321,12 +322,20 @@ class Params:
         p.elbow_thresh, p.target_sparsity, p.conv_tol = self.elbow_thresh, self.target_sparsity, self.conv_tol
         p.max_iter, p.fixed_pr_mode, p.fixed_pr = self.max_iter, self.fixed_pr_mode, self.fixed_pr
         p.count_mode, p.normalize, p.revive_on_stop = self.count_mode, self.normalize, self.revive_on_stop
+        p.resume = self.resume
         return p
 
 
-def autosearch(prob: Problem, model: Model, params: Params) -> dict:
+def autosearch(prob: Problem, model: Model, params: Params, resume_from: dict | None = None) -> dict:
+    """Algorithm 2 on `model` in place.  With params.resume, `resume_from` is the report of the
+    run being continued (as returned by an earlier call)."""
     t, m, p = prob.cstruct(), model.cstruct(), params.cstruct()
     rep = _Report()
+    if resume_from is not None:
+        k = int(resume_from["iters"])
+        rep.iters, rep.stop_iter = k, int(resume_from["stop_iter"])
+        for name, key in (("re_hist", "re"), ("obj_hist", "obj"), ("pr_hist", "pr"), ("sparsity_hist", "sparsity")):
+            getattr(rep, name)[:k] = [float(v) for v in resume_from[key][:k]]
     _check(lib().or_autosearch(C.byref(t), C.byref(m), C.byref(p), C.byref(rep)), "autosearch")
     it = rep.iters
     return {"iters": it, "stop_iter": rep.stop_iter, "re": np.array(rep.re_hist[:it]),

@@ -474,10 +474,16 @@ double or_elbow_stat(double re_t, double re_t1, double re_t2, double pr_t) {
  *   - revive_on_stop (VeST_auto only; the paper describes it and leaves it
  *     out of its runs): when the elbow rule fires, the masks go back to what
  *     they were before the last pruning step, so the elements that step
- *     removed are unpruned; they hold 0 until the next sweep refits them. */
+ *     removed are unpruned; they hold 0 until the next sweep refits them;
+ *   - resume: the loop continues from iteration rep->iters + 1 with the
+ *     report's histories, and pruning continues unless rep->stop_iter is set.
+ *     A run of K iterations without normalisation, resumed to max_iter,
+ *     equals one run to max_iter (the revive step only sees prunes made
+ *     after the resume). */
 int or_autosearch(const or_tensor* t, or_model* m, const or_params* p, or_report* rep) {
   if (!valid(t, m) || !p || !rep || p->max_iter < 1 || p->max_iter > 256) return OR_ERR_INVALID;
-  memset(rep, 0, sizeof(*rep));
+  if (p->resume && (rep->iters < 0 || rep->iters > 256)) return OR_ERR_INVALID;
+  if (!p->resume) memset(rep, 0, sizeof(*rep));
   const int64_t gs = core_size(m);
   double* df[OR_MAX_ORDER] = {0};
   double* dc = (double*)malloc((size_t)gs * sizeof(double));
@@ -486,7 +492,7 @@ int or_autosearch(const or_tensor* t, or_model* m, const or_params* p, or_report
     df[n] = (double*)malloc((size_t)(m->I[n] * m->J[n]) * sizeof(double));
     if (!df[n]) rc = OR_ERR_NOMEM;
   }
-  int pruning = 1, saved = 0;
+  int pruning = p->resume ? rep->stop_iter == 0 : 1, saved = 0;
   const int revive = p->revive_on_stop && p->target_sparsity < 0.0;
   uint8_t* keep[OR_MAX_ORDER + 1] = {0}; /* masks before the last pruning step */
   for (int32_t n = 0; revive && n <= m->N && rc == OR_OK; ++n) {
@@ -495,7 +501,7 @@ int or_autosearch(const or_tensor* t, or_model* m, const or_params* p, or_report
     if (!keep[n]) rc = OR_ERR_NOMEM;
   }
   double out[5];
-  for (int32_t it = 1; rc == OR_OK && it <= p->max_iter; ++it) {
+  for (int32_t it = p->resume ? rep->iters + 1 : 1; rc == OR_OK && it <= p->max_iter; ++it) {
     rc = or_sweep_factors(t, m, p->reg, p->lambda, -1);
     if (rc == OR_OK) rc = or_sweep_core(t, m, p->reg, p->lambda);
     if (rc == OR_OK) rc = or_loss(t, m, p->reg, p->lambda, out);

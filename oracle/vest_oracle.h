@@ -60,6 +60,8 @@ typedef struct {
   int32_t normalize;      /* 1: final column normalisation */
   int32_t revive_on_stop; /* VeST_auto only: when the elbow rule stops pruning, the elements
                              pruned by the last pruning step are unpruned again (Section 3.1) */
+  int32_t resume;         /* 1: continue the run recorded in the report passed in (iters done,
+                             histories, stop_iter) on the model as it stands */
 } or_params;
 
 typedef struct {

@@ -414,7 +414,8 @@ vest_status vest_autosearch(const vest_index* ix, vest_model* m, const vest_para
   VEST_TRY(check_scratch(ix, m, scratch, scratch_bytes, &plan));
   const cudaStream_t s = as_stream(stream);
   char* sc = static_cast<char*>(scratch);
-  std::memset(rep, 0, sizeof(*rep));
+  if (p->resume && (rep->iters < 0 || rep->iters > 256)) return fail(VEST_ERR_INVALID, "resumed report: iters must be in [0, 256]");
+  if (!p->resume) std::memset(rep, 0, sizeof(*rep));
   double* loss = reinterpret_cast<double*>(sc + plan.off_small) + kSmallLoss;
   int64_t* zeros = reinterpret_cast<int64_t*>(reinterpret_cast<double*>(sc + plan.off_small) + kSmallZeros);
   // the Delta scores of every element follow the planned regions of the scratch
@@ -457,8 +458,8 @@ vest_status vest_autosearch(const vest_index* ix, vest_model* m, const vest_para
     *out_sp = (double)z / total_size;
     return VEST_OK;
   };
-  bool pruning = true;
-  for (int it = 1; it <= p->max_iter; ++it) {
+  bool pruning = p->resume ? rep->stop_iter == 0 : true;
+  for (int it = p->resume ? rep->iters + 1 : 1; it <= p->max_iter; ++it) {
     // the sweeps leave the residual of the swept model in the scratch: the loss and, when
     // this iteration prunes, the responsibility read it instead of recomputing B
     VEST_TRY(iteration_sweeps(ix, m, p->reg, p->lambda, 1, loss, scratch, scratch_bytes, plan, stream));

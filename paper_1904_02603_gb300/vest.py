@@ -51,7 +51,8 @@ class vest_params(C.Structure):
     _fields_ = [("reg", C.c_int32), ("lambda_", C.c_double), ("init_pr", C.c_double), ("max_pr", C.c_double),
                 ("elbow_thresh", C.c_double), ("target_sparsity", C.c_double), ("conv_tol", C.c_double),
                 ("max_iter", C.c_int32), ("fixed_pr_mode", C.c_int32), ("fixed_pr", C.c_double),
-                ("count_mode", C.c_int32), ("normalize", C.c_int32), ("revive_on_stop", C.c_int32)]
+                ("count_mode", C.c_int32), ("normalize", C.c_int32), ("revive_on_stop", C.c_int32),
+                ("resume", C.c_int32)]
 
 
 class vest_report(C.Structure):
@@ -410,17 +411,24 @@ def vest_reconstruct(m: Model, q_idx: torch.Tensor, stream=None) -> torch.Tensor
 
 def params(reg=REG_LF, lam=0.01, init_pr=0.01, max_pr=0.1, elbow_thresh=0.05, target_sparsity=-1.0,
            conv_tol=1e-6, max_iter=50, fixed_pr_mode=0, fixed_pr=0.0, count_mode=1, normalize=1,
-           revive_on_stop=0) -> vest_params:
+           revive_on_stop=0, resume=0) -> vest_params:
     p = vest_params()
     p.reg, p.lambda_, p.init_pr, p.max_pr = reg, lam, init_pr, max_pr
     p.elbow_thresh, p.target_sparsity, p.conv_tol, p.max_iter = elbow_thresh, target_sparsity, conv_tol, max_iter
     p.fixed_pr_mode, p.fixed_pr, p.count_mode, p.normalize = fixed_pr_mode, fixed_pr, count_mode, normalize
-    p.revive_on_stop = revive_on_stop
+    p.revive_on_stop, p.resume = revive_on_stop, resume
     return p
 
 
-def vest_autosearch(ix: Index, m: Model, p: vest_params, scratch: torch.Tensor, stream=None) -> dict:
+def vest_autosearch(ix: Index, m: Model, p: vest_params, scratch: torch.Tensor, stream=None,
+                    resume_from: dict | None = None) -> dict:
+    """Algorithm 2 on `m` in place; with p.resume, `resume_from` is the report being continued."""
     rep = vest_report()
+    if resume_from is not None:
+        k = int(resume_from["iters"])
+        rep.iters, rep.stop_iter = k, int(resume_from["stop_iter"])
+        for name, key in (("re_hist", "re"), ("obj_hist", "obj"), ("pr_hist", "pr"), ("sparsity_hist", "sparsity")):
+            getattr(rep, name)[:k] = [float(v) for v in resume_from[key][:k]]
     _call("vest_autosearch", ix.handle, C.byref(m.cstruct()), C.byref(p), C.byref(rep), _dptr(scratch),
           scratch.numel(), _stream(stream))
     it = rep.iters

@@ -221,6 +221,36 @@ def test_autosearch_revive_on_stop_f64():
     assert model_err(mdl, om) < TOL64
 
 
+def test_autosearch_resume_from_checkpoint_f64(tmp_path):
+    """A run stopped after 5 iterations, checkpointed to a file, loaded and resumed to 12 ends
+    bitwise where one run to 12 ends, and both match the oracle's uninterrupted run."""
+    from paper_1904_02603_gb300 import checkpoint
+    t, st = datagen.random_problem(42, (30, 25, 20), (3, 3, 3), 3000)
+    ten, whole = device_pair(t, st)
+    ix = V.vest_build_index(ten)
+    sc = V.make_scratch(ix, whole, autosearch=True)
+    kw = dict(reg=V.REG_LF, lam=0.05, init_pr=0.05, max_pr=0.2, target_sparsity=0.5, conv_tol=1e-9)
+    rep_whole = V.vest_autosearch(ix, whole, V.params(max_iter=12, normalize=1, **kw), sc)
+    _, part = device_pair(t, st)
+    first = V.vest_autosearch(ix, part, V.params(max_iter=5, normalize=0, **kw), sc)
+    checkpoint.save(tmp_path / "run.npz", part, first)
+    del part
+    resumed, rep0 = checkpoint.load(tmp_path / "run.npz")
+    rep = V.vest_autosearch(ix, resumed, V.params(max_iter=12, normalize=1, resume=1, **kw), sc, resume_from=rep0)
+    assert rep["iters"] == rep_whole["iters"] == 12 and rep["stop_iter"] == rep_whole["stop_iter"]
+    for key in ("re", "obj", "pr", "sparsity"):
+        np.testing.assert_array_equal(rep[key], rep_whole[key])
+    for a, b in zip(resumed.to_host(), whole.to_host()):
+        for x, y in zip(a if isinstance(a, list) else [a], b if isinstance(b, list) else [b]):
+            np.testing.assert_array_equal(x, y)
+    prob, om = oracle_pair(t, st)
+    orep = O.autosearch(prob, om, O.Params(max_iter=12, normalize=1, **{k: v for k, v in kw.items()}))
+    assert orep["stop_iter"] == rep["stop_iter"]
+    assert rel_err(rep["re"], orep["re"]) < TOL64
+    assert masks_equal(resumed, om)
+    assert model_err(resumed, om) < TOL64
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_value_pruning_keys_and_prune(dtype):
     """Value Pruning: |element| keys bit-exact, then the 60 % smallest per segment pruned as the

@@ -412,6 +412,30 @@ def test_autosearch_revive_restores_the_masks_before_the_last_prune(oracle_lib):
     assert rev["sparsity"][k] == plain["sparsity"][k - 3] < plain["sparsity"][k]
 
 
+@pytest.mark.parametrize("split", [5, 8])
+def test_autosearch_resume_equals_one_run(oracle_lib, split):
+    """A run stopped after `split` iterations (no normalisation) and resumed from its report to
+    max_iter gives the same report and model as one run to max_iter; the manual-mode stop falls
+    at iteration 6, so the two splits resume before and after it."""
+    def params(max_iter, normalize, resume):
+        return O.Params(reg=O.REG_LF, lam=0.05, init_pr=0.05, max_pr=0.2, target_sparsity=0.5, max_iter=max_iter,
+                        conv_tol=1e-9, normalize=normalize, resume=resume)
+
+    prob, one = small_problem(42, (30, 25, 20), (3, 3, 3), 3000)
+    whole = O.autosearch(prob, one, params(12, 1, 0))
+    _, two = small_problem(42, (30, 25, 20), (3, 3, 3), 3000)
+    first = O.autosearch(prob, two, params(split, 0, 0))
+    assert first["iters"] == split and whole["stop_iter"] == 6
+    rest = O.autosearch(prob, two, params(12, 1, 1), resume_from=first)
+    assert rest["iters"] == whole["iters"] and rest["stop_iter"] == whole["stop_iter"]
+    for key in ("re", "obj", "pr", "sparsity"):
+        np.testing.assert_array_equal(rest[key], whole[key])
+    for a, b in zip(one.A + [one.G], two.A + [two.G]):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(one.Amask + [one.Gmask], two.Amask + [two.Gmask]):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_planted_model_is_recovered(oracle_lib):
     # noiseless, fully observed, rank-matched: CD drives RE towards 0 (a sanity check,
     # not a pin: the problem is non-convex and some starts plateau for a long time)
