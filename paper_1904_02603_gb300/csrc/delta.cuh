@@ -84,99 +84,11 @@ __global__ void prep_core_kernel(const T* __restrict__ G, ModeRoles r, int JN, T
   }
 }
 
-// ---------------------------------------------------------------- vector loads of JN core values
-template <typename T, int JN>
-__device__ __forceinline__ void fma_row(T (&d)[JN], T w, const T* __restrict__ g) {
-  if constexpr (sizeof(T) == 4 && JN % 4 == 0) {
-#pragma unroll
-    for (int j = 0; j < JN; j += 4) {
-      const float4 v = *reinterpret_cast<const float4*>(g + j);
-      d[j + 0] = fmaf(w, v.x, d[j + 0]);
-      d[j + 1] = fmaf(w, v.y, d[j + 1]);
-      d[j + 2] = fmaf(w, v.z, d[j + 2]);
-      d[j + 3] = fmaf(w, v.w, d[j + 3]);
-    }
-  } else if constexpr (sizeof(T) == 4 && JN % 2 == 0) {
-#pragma unroll
-    for (int j = 0; j < JN; j += 2) {
-      const float2 v = *reinterpret_cast<const float2*>(g + j);
-      d[j + 0] = fmaf(w, v.x, d[j + 0]);
-      d[j + 1] = fmaf(w, v.y, d[j + 1]);
-    }
-  } else if constexpr (sizeof(T) == 8 && JN % 2 == 0) {
-#pragma unroll
-    for (int j = 0; j < JN; j += 2) {
-      const double2 v = *reinterpret_cast<const double2*>(g + j);
-      d[j + 0] = fma(w, v.x, d[j + 0]);
-      d[j + 1] = fma(w, v.y, d[j + 1]);
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < JN; ++j) d[j] = d[j] + w * g[j];
-  }
-}
-
 // Slow-mode row pointers and ranks for one entry.
 struct SlowRows {
   const void* row[kMaxOrder];
   int J[kMaxOrder];
 };
-
-// delta for one entry.  NSLOW = number of slow modes when fixed at compile
-// time (0, 1, 2), or -1 for a runtime count.
-template <typename T, int JN, int NSLOW>
-__device__ __forceinline__ void compute_delta(T (&d)[JN], const T* __restrict__ g, const uint8_t* __restrict__ onz,
-                                              int64_t n_outer, int Jf, const T* __restrict__ rowf,
-                                              const SlowRows& sr, int nslow) {
-#pragma unroll
-  for (int j = 0; j < JN; ++j) d[j] = T(0);
-  const int64_t slice = (int64_t)Jf * JN;
-  if constexpr (NSLOW == 0) {
-    for (int cf = 0; cf < Jf; ++cf) fma_row<T, JN>(d, __ldg(rowf + cf), g + cf * JN);
-  } else if constexpr (NSLOW == 1) {
-    const T* r0 = static_cast<const T*>(sr.row[0]);
-    for (int o = 0; o < (int)n_outer; ++o) {
-      if (!onz[o]) continue;
-      const T w = __ldg(r0 + o);
-      if (w == T(0)) continue;
-      const T* go = g + o * slice;
-      for (int cf = 0; cf < Jf; ++cf) fma_row<T, JN>(d, w * __ldg(rowf + cf), go + cf * JN);
-    }
-  } else if constexpr (NSLOW == 2) {
-    const T* r0 = static_cast<const T*>(sr.row[0]);
-    const T* r1 = static_cast<const T*>(sr.row[1]);
-    const int J0 = sr.J[0], J1 = sr.J[1];
-    for (int d1 = 0; d1 < J1; ++d1) {
-      const T w1 = __ldg(r1 + d1);
-      if (w1 == T(0)) continue;
-      for (int d0 = 0; d0 < J0; ++d0) {
-        const int o = d0 + J0 * d1;
-        if (!onz[o]) continue;
-        const T w = w1 * __ldg(r0 + d0);
-        if (w == T(0)) continue;
-        const T* go = g + o * slice;
-        for (int cf = 0; cf < Jf; ++cf) fma_row<T, JN>(d, w * __ldg(rowf + cf), go + cf * JN);
-      }
-    }
-  } else {
-    int dig[kMaxOrder];
-    for (int i = 0; i < nslow; ++i) dig[i] = 0;
-    for (int64_t o = 0; o < n_outer; ++o) {
-      if (onz[o]) {
-        T w = T(1);
-        for (int i = 0; i < nslow; ++i) w *= __ldg(static_cast<const T*>(sr.row[i]) + dig[i]);
-        if (w != T(0)) {
-          const T* go = g + o * slice;
-          for (int cf = 0; cf < Jf; ++cf) fma_row<T, JN>(d, w * __ldg(rowf + cf), go + cf * JN);
-        }
-      }
-      for (int i = 0; i < nslow; ++i) {  // odometer, slow[0] fastest
-        if (++dig[i] < sr.J[i]) break;
-        dig[i] = 0;
-      }
-    }
-  }
-}
 
 // ---------------------------------------------------------------- delta for E entries at once
 // The core fibre of each (o, j_f) is read from shared memory once and feeds all
@@ -532,17 +444,6 @@ __device__ void piece_sums(const int64_t* sptr, int nrows, int64_t t0, int64_t t
     }
   }
   __syncthreads();
-}
-
-// local row of position p: largest q < nrows with sptr[q] <= p
-__device__ __forceinline__ int local_row(const int64_t* sptr, int nrows, int64_t p) {
-  int lo = 0, hi = nrows - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (sptr[mid] <= p) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
 }
 
 }  // namespace vest
