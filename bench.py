@@ -510,7 +510,7 @@ def main_sparsity_curve(args):
     clocks = ClockSampler(gpu_index_for_smi(0))
     for reg_name, reg in (("LF", V.REG_LF), ("L1", V.REG_L1)):
         rows = []
-        for target in list(SPARSITY_TARGETS) + [-1.0]:
+        for target, rise in [(x, 0) for x in SPARSITY_TARGETS] + [(-1.0, 0), (-1.0, 1)]:
             mdl = V.Model.from_host(st)
             sc = V.make_scratch(ix_tr, mdl, autosearch=True)
             sc_te = V.make_scratch(ix_te, mdl)
@@ -518,14 +518,15 @@ def main_sparsity_curve(args):
             l0 = V.vest_launch_count()
             t0 = time.perf_counter()
             rep = V.vest_autosearch(ix_tr, mdl, V.params(reg=reg, lam=w.lam, target_sparsity=target,
-                                                         max_iter=max_iter), sc)
+                                                         max_iter=max_iter, elbow_rise=rise), sc)
             torch.cuda.synchronize()
             secs = time.perf_counter() - t0
             launches += V.vest_launch_count() - l0
             total_s += secs
             tr = V.vest_loss(ix_tr, mdl, reg, w.lam, sc).cpu().numpy()
             te = V.vest_loss(ix_te, mdl, reg, w.lam, sc_te).cpu().numpy()
-            rows.append({"target": None if target < 0 else target, "mode": "auto" if target < 0 else "man",
+            mode = "man" if target >= 0 else ("auto_rise" if rise else "auto")
+            rows.append({"target": None if target < 0 else target, "mode": mode,
                          "sparsity": rep["final_sparsity"], "re_train": float(tr[4]), "re_test": float(te[4]),
                          "iters": rep["iters"], "stop_iter": rep["stop_iter"], "seconds": secs})
             if target == 0.0:  # Value Pruning: the unpruned fit, then |value| keys at ratio 0.6
@@ -549,7 +550,8 @@ def main_sparsity_curve(args):
         "config": {**workload_config(w), "workload": SPARSITY, "tensor": w.name, "test_fraction": 0.1,
                    "max_iter": max_iter, "truth_sparsity": truth_sparsity,
                    "schedule": "pr_t = min(0.01 t, 0.1) of all elements; VeST_man stops pruning at the target, "
-                               "VeST_auto at the elbow (threshold 0.05); value_pruning: the s = 0 fit with the 60 % "
+                               "VeST_auto at the elbow (threshold 0.05; auto_rise also needs RE to rise); "
+                               "value_pruning: the s = 0 fit with the 60 % "
                                "smallest |element| of each segment pruned, no refit"},
         "curves": curves,
         "seconds_total": total_s,

@@ -125,6 +125,8 @@ typedef struct {
                              the elements the last pruning step removed (Section 3.1) */
   int32_t resume;         /* 1: continue the run recorded in the report passed in (a checkpoint:
                              iters done, histories, stop_iter) on the model as it stands */
+  int32_t elbow_rise;     /* VeST_auto, 1: the elbow also needs RE_t > RE_{t-1} (Section 3.1
+                             describes the stop as a rapid increase of the error) */
 } vest_params;
 
 typedef struct {
@@ -229,7 +231,8 @@ vest_status vest_count_zeros(const vest_model* m, int64_t* out, void* scratch, s
  * core sweep, RE, and, while should_prune(), responsibility + prune with
  * pr_t = min(init_pr * t, max_pr) (t = 1, 2, ...) or fixed_pr.  VeST_man
  * stops pruning once the sparsity reaches target_sparsity; VeST_auto stops
- * the first time t >= 3 and (RE_t + RE_{t-2} - 2 RE_{t-1}) / pr_t > elbow_thresh.
+ * the first time t >= 3 and (RE_t + RE_{t-2} - 2 RE_{t-1}) / pr_t > elbow_thresh
+ * (and, with elbow_rise, RE_t > RE_{t-1}).
  * With revive_on_stop (VeST_auto), the masks return to their state before
  * the last pruning step when the elbow rule fires; the revived elements hold 0
  * until the next sweep refits them.  With resume, the loop continues from

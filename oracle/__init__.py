@@ -66,7 +66,7 @@ class _Params(C.Structure):
                 ("max_pr", C.c_double), ("elbow_thresh", C.c_double), ("target_sparsity", C.c_double),
                 ("conv_tol", C.c_double), ("max_iter", C.c_int32), ("fixed_pr_mode", C.c_int32),
                 ("fixed_pr", C.c_double), ("count_mode", C.c_int32), ("normalize", C.c_int32),
-                ("revive_on_stop", C.c_int32), ("resume", C.c_int32)]
+                ("revive_on_stop", C.c_int32), ("resume", C.c_int32), ("elbow_rise", C.c_int32)]
 
 
 class _Report(C.Structure):
@@ -315,6 +315,7 @@ class Params:
     normalize: int = 1
     revive_on_stop: int = 0
     resume: int = 0
+    elbow_rise: int = 0
 
     def cstruct(self):
         p = _Params()
@@ -322,7 +323,7 @@ class Params:
         p.elbow_thresh, p.target_sparsity, p.conv_tol = self.elbow_thresh, self.target_sparsity, self.conv_tol
         p.max_iter, p.fixed_pr_mode, p.fixed_pr = self.max_iter, self.fixed_pr_mode, self.fixed_pr
         p.count_mode, p.normalize, p.revive_on_stop = self.count_mode, self.normalize, self.revive_on_stop
-        p.resume = self.resume
+        p.resume, p.elbow_rise = self.resume, self.elbow_rise
         return p
 
 

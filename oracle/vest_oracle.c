@@ -468,7 +468,11 @@ double or_elbow_stat(double re_t, double re_t1, double re_t2, double pr_t) {
  *     would prune nothing), or fixed_pr when fixed_pr_mode is set;
  *   - VeST_man stops pruning once the sparsity reaches the target;
  *   - VeST_auto stops pruning, for good, the first time t >= 3 and
- *     (RE_t + RE_{t-2} - 2 RE_{t-1}) / pr_t exceeds the threshold;
+ *     (RE_t + RE_{t-2} - 2 RE_{t-1}) / pr_t exceeds the threshold; with
+ *     elbow_rise also RE_t > RE_{t-1} is required, reading Section 3.1's
+ *     "rapid increase" of the error into the rule (a falling RE with a large
+ *     second difference, as in the first sweeps from a random start, is then
+ *     no elbow);
  *   - the loop ends at max_iter, or once pruning has stopped and
  *     |RE_{t-1} - RE_t| <= conv_tol * RE_{t-1};
  *   - revive_on_stop (VeST_auto only; the paper describes it and leaves it
@@ -514,7 +518,7 @@ int or_autosearch(const or_tensor* t, or_model* m, const or_params* p, or_report
       const double pr = p->fixed_pr_mode ? p->fixed_pr : fmin(p->init_pr * it, p->max_pr);
       if (p->target_sparsity >= 0.0) {
         if (or_sparsity(m) >= p->target_sparsity) pruning = 0;
-      } else if (it >= 3 &&
+      } else if (it >= 3 && (!p->elbow_rise || out[4] > rep->re_hist[h - 1]) &&
                  or_elbow_stat(out[4], rep->re_hist[h - 1], rep->re_hist[h - 2], pr) > p->elbow_thresh) {
         pruning = 0;
       }

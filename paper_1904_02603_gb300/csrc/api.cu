@@ -477,7 +477,7 @@ vest_status vest_autosearch(const vest_index* ix, vest_model* m, const vest_para
         double sp;
         VEST_TRY(sparsity(&sp));
         if (sp >= p->target_sparsity) pruning = false;
-      } else if (it >= 3 &&
+      } else if (it >= 3 && (!p->elbow_rise || hl[4] > rep->re_hist[h - 1]) &&
                  (hl[4] + rep->re_hist[h - 2] - 2.0 * rep->re_hist[h - 1]) / pr > p->elbow_thresh) {
         pruning = false;
       }

@@ -52,7 +52,7 @@ class vest_params(C.Structure):
                 ("elbow_thresh", C.c_double), ("target_sparsity", C.c_double), ("conv_tol", C.c_double),
                 ("max_iter", C.c_int32), ("fixed_pr_mode", C.c_int32), ("fixed_pr", C.c_double),
                 ("count_mode", C.c_int32), ("normalize", C.c_int32), ("revive_on_stop", C.c_int32),
-                ("resume", C.c_int32)]
+                ("resume", C.c_int32), ("elbow_rise", C.c_int32)]
 
 
 class vest_report(C.Structure):
@@ -411,12 +411,12 @@ def vest_reconstruct(m: Model, q_idx: torch.Tensor, stream=None) -> torch.Tensor
 
 def params(reg=REG_LF, lam=0.01, init_pr=0.01, max_pr=0.1, elbow_thresh=0.05, target_sparsity=-1.0,
            conv_tol=1e-6, max_iter=50, fixed_pr_mode=0, fixed_pr=0.0, count_mode=1, normalize=1,
-           revive_on_stop=0, resume=0) -> vest_params:
+           revive_on_stop=0, resume=0, elbow_rise=0) -> vest_params:
     p = vest_params()
     p.reg, p.lambda_, p.init_pr, p.max_pr = reg, lam, init_pr, max_pr
     p.elbow_thresh, p.target_sparsity, p.conv_tol, p.max_iter = elbow_thresh, target_sparsity, conv_tol, max_iter
     p.fixed_pr_mode, p.fixed_pr, p.count_mode, p.normalize = fixed_pr_mode, fixed_pr, count_mode, normalize
-    p.revive_on_stop, p.resume = revive_on_stop, resume
+    p.revive_on_stop, p.resume, p.elbow_rise = revive_on_stop, resume, elbow_rise
     return p
 
 

@@ -221,6 +221,24 @@ def test_autosearch_revive_on_stop_f64():
     assert model_err(mdl, om) < TOL64
 
 
+def test_autosearch_elbow_rise_f64():
+    """VeST_auto with elbow_rise against the oracle: pruning runs until RE rises (iteration 11 on
+    this problem), not just until its second difference is large."""
+    t, st = datagen.random_problem(42, (30, 25, 20), (3, 3, 3), 3000)
+    ten, mdl = device_pair(t, st)
+    ix = V.vest_build_index(ten)
+    sc = V.make_scratch(ix, mdl, autosearch=True)
+    kw = dict(reg=V.REG_LF, lam=0.05, max_iter=20, conv_tol=1e-7, normalize=1, elbow_rise=1)
+    rep = V.vest_autosearch(ix, mdl, V.params(**kw), sc)
+    prob, om = oracle_pair(t, st)
+    orep = O.autosearch(prob, om, O.Params(**kw))
+    assert rep["stop_iter"] == orep["stop_iter"] > 3 and rep["iters"] == orep["iters"]
+    assert rel_err(rep["re"], orep["re"]) < TOL64
+    np.testing.assert_array_equal(rep["sparsity"], orep["sparsity"])
+    assert masks_equal(mdl, om)
+    assert model_err(mdl, om) < TOL64
+
+
 def test_autosearch_resume_from_checkpoint_f64(tmp_path):
     """A run stopped after 5 iterations, checkpointed to a file, loaded and resumed to 12 ends
     bitwise where one run to 12 ends, and both match the oracle's uninterrupted run."""

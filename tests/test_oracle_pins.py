@@ -387,6 +387,24 @@ def test_autosearch_auto_mode_stops_at_first_elbow(oracle_lib):
     assert rep["stop_iter"] == (fire or 0)
 
 
+def test_autosearch_elbow_rise_waits_for_a_rising_error(oracle_lib):
+    """With elbow_rise the stop is the first t >= 3 whose second difference exceeds the threshold
+    while RE_t > RE_{t-1}; RE falls at every pruned iteration before it."""
+    prob, model = small_problem(42, (30, 25, 20), (3, 3, 3), 3000)
+    p = O.Params(reg=O.REG_LF, lam=0.05, target_sparsity=-1.0, max_iter=30, conv_tol=1e-7, normalize=0, elbow_rise=1)
+    rep = O.autosearch(prob, model, p)
+    re = rep["re"]
+    fire = None
+    for t in range(3, rep["iters"] + 1):
+        pr = min(0.01 * t, 0.1)
+        if re[t - 1] > re[t - 2] and (re[t - 1] + re[t - 3] - 2 * re[t - 2]) / pr > 0.05:
+            fire = t
+            break
+    assert fire is not None and rep["stop_iter"] == fire
+    assert np.all(np.diff(re[:fire - 1]) < 0)
+    assert rep["sparsity"][fire - 2] > rep["sparsity"][1]  # pruning went on past the early sweeps
+
+
 def test_autosearch_revive_restores_the_masks_before_the_last_prune(oracle_lib):
     """VeST_auto with revive_on_stop: when the elbow fires at iteration k, the masks go back to
     those after iteration k-2 (before the prune of iteration k-1); the run up to k is unchanged."""
