@@ -340,3 +340,16 @@ def split_entries(t: SparseTensor, test_fraction: float = 0.1, seed: int = 1005)
 SPARSITY_CURVE = Workload("planted_1000x3_1e6", (1000, 1000, 1000), (10, 10, 10), 1_000_000, "uniform",
                           core_density=0.1, factor_density=0.3, noise=0.01, dtype="f32", reg="LF", lam=0.01,
                           data_seed=1006, init_seed=2006)
+
+
+# ---------------------------------------------------------------- pruning scores for selection tests
+def tied_scores(sizes, seed: int) -> list:
+    """One float64 score array per segment size: values on a coarse grid (many ties), a tenth of
+    them negative and some -0.0, so a selection by (score, index) meets every ordering case."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for size in sizes:
+        v = np.round(rng.standard_normal(int(size)) * 50.0) / 10.0
+        v[rng.random(int(size)) < 0.01] = -0.0
+        out.append(v.astype(np.float64))
+    return out
