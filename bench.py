@@ -70,7 +70,7 @@ def workload_config(w: datagen.Workload, extra=None):
     c = {"workload": w.name, "dims": list(w.dims), "ranks": list(w.ranks), "nnz": w.nnz, "index_dist": w.dist,
          "zipf_s": w.zipf_s if w.dist == "zipf" else None, "reg": w.reg, "lambda": w.lam,
          "core_density_planted": w.core_density, "factor_density_planted": w.factor_density, "noise": w.noise,
-         "init": "U(0,1) dense (Algorithm 2, line 1)", "data_seed": w.data_seed, "init_seed": w.init_seed}
+         "init": "U(0,1) dense (the random start of Algorithm 2)", "data_seed": w.data_seed, "init_seed": w.init_seed}
     if extra:
         c.update(extra)
     return c

@@ -120,7 +120,7 @@ typedef struct {
   int32_t fixed_pr_mode;  /* 1: prune fixed_pr at every pruning step */
   double fixed_pr;
   int32_t count_mode;     /* 0: k = floor(pr * #unpruned); 1: k = floor(pr * size) */
-  int32_t normalize;      /* 1: final column normalisation (Algorithm 2, last loop) */
+  int32_t normalize;      /* 1: final column normalisation (end of Algorithm 2) */
   int32_t revive_on_stop; /* VeST_auto only, 1: when the elbow rule stops pruning, unprune
                              the elements the last pruning step removed (Section 3.1) */
   int32_t resume;         /* 1: continue the run recorded in the report passed in (a checkpoint:
@@ -196,7 +196,7 @@ vest_status vest_responsibility(const vest_index* ix, const vest_model* m, doubl
                                 double* delta_core, double* const* resp_factor, double* resp_core,
                                 void* scratch, size_t scratch_bytes, void* stream);
 
-/* ---- a8: prune (Section 3.3; last step of Algorithm 3).  For each A^(n) and
+/* ---- a8: prune (Section 3.3; the pruning step of Algorithm 3).  For each A^(n) and
  * for G separately, among unpruned elements select the k smallest Delta
  * (ties: smaller linear index first; -0 == +0), k = floor(pr * #unpruned)
  * (count_mode 0) or floor(pr * size) (count_mode 1), capped at #unpruned; or,
@@ -218,7 +218,7 @@ vest_status vest_prune(vest_model* m, double* const* delta_factor, const double*
  * caller-owned; NULL outputs give VEST_ERR_INVALID.  Never synchronises. */
 vest_status vest_value_keys(const vest_model* m, double* const* key_factor, double* key_core, void* stream);
 
-/* ---- a9: normalisation (Algorithm 2, last loop): A^(n) = U^(n) B^(n) with
+/* ---- a9: normalisation (the final step of Algorithm 2): A^(n) = U^(n) B^(n) with
  * unit-norm columns, A^(n) <- U^(n), G <- G x_n B^(n); zero columns stay 0. */
 vest_status vest_normalize(vest_model* m, void* scratch, size_t scratch_bytes, void* stream);
 
@@ -250,7 +250,7 @@ size_t vest_autosearch_scratch_bytes(const vest_index* ix, const vest_model* m);
 vest_status vest_autosearch(const vest_index* ix, vest_model* m, const vest_params* p, vest_report* report,
                             void* scratch, size_t scratch_bytes, void* stream);
 
-/* ---- a2-a8 in one call: one iteration of Algorithm 2 (lines 3-9): factor
+/* ---- a2-a8 in one call: one iteration of the loop of Algorithm 2: factor
  * sweep over every mode (skipped when factor_sweep is 0, for callers that
  * sweep the modes themselves), core sweep, loss of the swept model, and, when
  * delta_factor is not NULL, the responsibility of every element (Eq. 5/6) and

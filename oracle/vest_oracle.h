@@ -95,7 +95,7 @@ int or_sweep_core(const or_tensor* t, or_model* m, int32_t reg, double lambda);
 /* Definition 1-2, Eq. 3-6, Algorithm 3 (scores only) */
 int or_responsibility(const or_tensor* t, const or_model* m, double* const* delta_factor,
                       double* delta_core, double* const* resp_factor, double* resp_core);
-/* Pruning with the marking table (Section 3.3, Algorithm 3 last step) */
+/* Pruning with the marking table (Section 3.3, the pruning step of Algorithm 3) */
 int or_prune(or_model* m, double* const* delta_factor, const double* delta_core, double pr,
              int32_t count_mode, int32_t threshold_mode, double tau, int64_t* n_pruned);
 /* Algorithm 2, final loop: unit-norm columns, core rescaled */

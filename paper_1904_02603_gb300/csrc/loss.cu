@@ -1,5 +1,5 @@
 // Loss / RE (Eq. 1, Eq. 2, Eq. 4), entry-wise reconstruction (Eq. 7),
-// column normalisation (Algorithm 2, last loop) and zero counts.
+// column normalisation (the final step of Algorithm 2) and zero counts.
 //
 // B(alpha) = sum_j a0[i_0, j] delta^(0)_alpha(j): the mode-0 delta of Eq. 11
 // dotted with the entry's mode-0 factor row, over the mode-0 CSR.  Products and

@@ -1,4 +1,4 @@
-// Pruning with the marking table (Section 3.3; last step of Algorithm 3).
+// Pruning with the marking table (Section 3.3; the pruning step of Algorithm 3).
 // Per segment (each A^(n), then G) the unpruned elements are ordered by
 // (Delta, linear index) and the first k = floor(pr * #candidates) (or
 // floor(pr * size)) are marked and zeroed.  The k-th pair is found by a radix

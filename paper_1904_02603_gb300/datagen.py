@@ -2,7 +2,7 @@
 
 This module only draws inputs: observed index sets, values from a *planted*
 sparse Tucker model plus Gaussian noise, and the U(0,1) initial state of the
-model being fitted (Algorithm 2, first line).  It is shared by the CUDA tests,
+model being fitted (the random start of Algorithm 2).  It is shared by the CUDA tests,
 the bench and the oracle tests, and holds none of the fitted method's
 arithmetic: no update rule, no responsibility, no pruning, no loss.  The one
 contraction here evaluates the planted ground-truth model to synthesise X.
@@ -184,7 +184,7 @@ def planted_values_on(device, idx: np.ndarray, planted: ModelState, noise: float
 
 
 def random_init(dims, ranks, seed: int, dtype=np.float64) -> ModelState:
-    """Algorithm 2, first line: every core and factor element drawn U(0,1)."""
+    """The random start of Algorithm 2: every core and factor element drawn U(0,1)."""
     rng = np.random.default_rng(seed)
     factors = [rng.random((int(d), int(r))).astype(dtype) for d, r in zip(dims, ranks)]
     core = rng.random(math.prod(ranks)).astype(dtype)
