@@ -126,7 +126,7 @@ typedef struct {
   int32_t resume;         /* 1: continue the run recorded in the report passed in (a checkpoint:
                              iters done, histories, stop_iter) on the model as it stands */
   int32_t elbow_rise;     /* VeST_auto, 1: the elbow also needs RE_t > RE_{t-1} (Section 3.1
-                             describes the stop as a rapid increase of the error) */
+                             describes the stop as the error climbing fast) */
 } vest_params;
 
 typedef struct {
@@ -210,7 +210,7 @@ vest_status vest_prune(vest_model* m, double* const* delta_factor, const double*
                        void* scratch, size_t scratch_bytes, void* stream);
 
 /* ---- Value Pruning keys (Section 4.1, competitors: VeST_man with s = 0, then
- * value pruning with ratio 0.6).  Writes |element| in FP64 for every element
+ * value pruning at ratio 0.6).  Writes |element| in FP64 for every element
  * of every segment: key_factor[n] is device double[I_n * J_n] row-major like
  * A^(n), key_core device double[prod J_n] like G.  Passing them to vest_prune
  * with pr = 0.6 and count_mode = 1 prunes, in each segment, the 60 % of its

@@ -470,9 +470,9 @@ double or_elbow_stat(double re_t, double re_t1, double re_t2, double pr_t) {
  *   - VeST_auto stops pruning, for good, the first time t >= 3 and
  *     (RE_t + RE_{t-2} - 2 RE_{t-1}) / pr_t exceeds the threshold; with
  *     elbow_rise also RE_t > RE_{t-1} is required, reading Section 3.1's
- *     "rapid increase" of the error into the rule (a falling RE with a large
- *     second difference, as in the first sweeps from a random start, is then
- *     no elbow);
+ *     description of the stop (the error climbing fast) into the rule: a
+ *     falling RE with a large second difference, as in the first sweeps from
+ *     a random start, is then no elbow;
  *   - the loop ends at max_iter, or once pruning has stopped and
  *     |RE_{t-1} - RE_t| <= conv_tol * RE_{t-1};
  *   - revive_on_stop (VeST_auto only; the paper describes it and leaves it

@@ -63,7 +63,7 @@ typedef struct {
   int32_t resume;         /* 1: continue the run recorded in the report passed in (iters done,
                              histories, stop_iter) on the model as it stands */
   int32_t elbow_rise;     /* VeST_auto, 1: the elbow also needs RE_t > RE_{t-1} (Section 3.1
-                             describes the stop as a rapid increase of the error) */
+                             describes the stop as the error climbing fast) */
 } or_params;
 
 typedef struct {
