@@ -116,7 +116,14 @@ def run_reference(args):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the one-tensor workloads only"}))
         return
     w = datagen.WORKLOADS[args.workload]
-    t, st, _ = datagen.make(w)
+    # the inputs are the same numbers either way; a device only forms the planted values faster
+    dev = None
+    try:
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else None
+    except ImportError:
+        pass
+    t, st, _ = datagen.make(w, device=dev)
     reg = 0 if w.reg == "LF" else 1
     per_step = min(10.0, 150.0 / max(args.steps + args.warmup, 1))
     dt, n = oracle_step_time(t, st, 4000, reg, w.lam)
