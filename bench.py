@@ -10,7 +10,13 @@ core sweep, loss, responsibility scores, prune.  This workload does not
 prune, so the prune runs its full selection with pr = 0 and changes nothing.
 value = (order * nnz) entry-mode updates per second of whole steps, all ranks.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
+
+Other workloads: uniform_1e4x4_5e7 (4-order, 5e7 entries, L_1), batch_256_jobs
+(independent jobs, batched against one at a time), serve_200rps (a request
+trace, p50/p99 latency), scalability (iteration time against order, mode size
+and entry count) and sparsity_curve (RE and held-out RE against the target
+sparsity).  --impl reference times the FP64 oracle on the host instead.
 
 With N > 1 (torchrun, one rank per GPU) every rank fits its own independent
 instance of the workload (weak scaling, no collective on the data path).
