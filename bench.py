@@ -5,10 +5,11 @@ Workload (default): 3-order 100,000^3 tensor, 1e7 observed entries with
 Zipf(1.2) indices per mode, FP32 values from a planted sparse Tucker model,
 ranks (10, 10, 10), L_F lambda = 0.01; the fitted model starts U(0,1) dense.
 
-One step = one pass of the whole path: factor sweep over every mode,
-core sweep, loss, responsibility scores, prune.  This workload does not
-prune, so the prune runs its full selection with pr = 0 and changes nothing.
-value = (order * nnz) entry-mode updates per second of whole steps, all ranks.
+One step = one iteration of Algorithm 2, the whole path: factor sweep over
+every mode, core sweep, loss, responsibility scores, and the prune at
+pr = 0.01 (the schedule's first rate, 1 % of each segment's unpruned
+elements).  value = (order * nnz) entry-mode updates per second of whole
+steps, all ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
 
