@@ -468,3 +468,37 @@ def test_planted_model_is_recovered(oracle_lib):
         O.sweep_factors(prob, model, O.REG_LF, 1e-6, -1)
         O.sweep_core(prob, model, O.REG_LF, 1e-6)
     assert O.loss(prob, model, O.REG_LF, 1e-6)[4] < 1e-2
+
+
+def test_ctypes_structs_match_the_oracle_header(tmp_path):
+    """Every field of the oracle's C structs, as gcc lays them out, equals its ctypes mirror."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not found")
+    pairs = [(O._Tensor, "or_tensor"), (O._Model, "or_model"), (O._Params, "or_params"), (O._Report, "or_report")]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vest_oracle.h"', "int main(void) {"]
+    for st, cname in pairs:
+        for name, _ in st._fields_:
+            field = "lambda" if name == "lambda_" else name
+            lines.append(f'  printf("{cname} {name} %zu %zu\\n", offsetof({cname}, {field}), '
+                         f"sizeof((({cname}*)0)->{field}));")
+        lines.append(f'  printf("{cname} SIZE %zu 0\\n", sizeof({cname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    here = os.path.dirname(os.path.abspath(O.__file__))
+    subprocess.run(["gcc", "-std=c11", "-I", here, str(src), "-o", str(exe)], check=True)
+    out = [x for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n") if x]
+    assert len(out) == sum(len(st._fields_) + 1 for st, _ in pairs)
+    by_name = {cname: st for st, cname in pairs}
+    for line in out:
+        cname, field, off, size = line.split()
+        st = by_name[cname]
+        if field == "SIZE":
+            assert C.sizeof(st) == int(off), cname
+        else:
+            f = getattr(st, field)
+            assert (f.offset, f.size) == (int(off), int(size)), (cname, field)
