@@ -54,3 +54,13 @@ def test_sparsity_curve_truth_sparsity():
     zeros = (1 - w.core_density) * math.prod(w.ranks) + (1 - w.factor_density) * sum(
         d * r for d, r in zip(w.dims, w.ranks))
     assert abs(zeros / elems - 0.71) < 0.01
+
+
+def test_planted_values_on_a_torch_device_are_the_same_numbers():
+    rng = np.random.default_rng(21)
+    dims, ranks = (40, 30, 20), (4, 3, 5)
+    idx = datagen.sample_indices(rng, dims, 3000)
+    planted = datagen.planted_model(rng, dims, ranks, 0.3, 0.5)
+    a = datagen.planted_values(idx, planted, 0.01, np.random.default_rng(5))
+    b = datagen.planted_values_on("cpu", idx, planted, 0.01, np.random.default_rng(5))
+    np.testing.assert_array_equal(a, b)
