@@ -1,10 +1,16 @@
-"""Whether the factors can be stored in BF16 (a variant considered for the 4-order workload):
+"""Precision studies behind two design choices, run on the CPU.
+
+1. Whether the factors can be stored in BF16 (a variant considered for the 4-order workload):
 one iteration of Algorithm 2's sweeps on the oracle, with the factor matrices rounded to the
 storage format after the factor sweep, against the same iteration kept in FP64.
 
 FP32 storage stays within 1e-6 of the FP64 objective; BF16 storage misses the 1e-4 relative
 objective tolerance of the FP32 path by more than ten times already after one iteration (and
-the gap grows over later iterations), so the library keeps FP32 factors."""
+the gap grows over later iterations), so the library keeps FP32 factors.
+
+2. Whether the delta contraction (Eq. 11) could move to the tensor cores in TF32: as one
+(entries x |G|/J_n) by (|G|/J_n x J_n) product with Khatri-Rao rows, one TF32 product errs by
+about 1e-4 relative while three (hi*hi + hi*lo + lo*hi, FP32 accumulation) match FP32 FMAs."""
 import numpy as np
 
 import oracle as O
@@ -16,6 +22,13 @@ def _round_bf16(a):
     u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
     r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _round_tf32(a):
+    """Round to the nearest TF32 value (10 explicit mantissa bits), ties to even, as FP32."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0xFFF + ((u >> 13) & 1)) >> 13) << 13
+    return r.astype(np.uint32).view(np.float32)
 
 
 def _round_fp32(a):
@@ -49,3 +62,19 @@ def test_bf16_factor_storage_misses_the_objective_tolerance():
     gap16 = abs(one_iteration(_round_bf16) - ref) / ref
     assert gap32 < 1e-6, gap32
     assert gap16 > 1e-3, gap16
+
+
+def test_three_tf32_products_match_fp32_on_the_delta_contraction():
+    rng = np.random.default_rng(0)
+    E, Jf, Jo, Jn = 4096, 10, 10, 10  # the 3-order rank-10 workload: |G|/J_n = 100
+    G = rng.random((Jo * Jf, Jn))  # permuted core of the U(0,1) start
+    A = (rng.random((E, Jo))[:, :, None] * rng.random((E, Jf))[:, None, :]).reshape(E, Jo * Jf)
+    ref = A @ G
+    A32, G32 = A.astype(np.float32), G.astype(np.float32)
+    err = lambda v: float((np.abs(v.astype(np.float64) - ref) / np.abs(ref)).max())
+    fp32 = err(A32 @ G32)
+    a_hi, g_hi = _round_tf32(A32), _round_tf32(G32)
+    a_lo, g_lo = _round_tf32(A32 - a_hi), _round_tf32(G32 - g_hi)
+    one = err(a_hi @ g_hi)
+    three = err(a_hi @ g_hi + a_hi @ g_lo + a_lo @ g_hi)
+    assert one > 1e-5 and three < 3 * fp32 and three < 2e-6, (fp32, one, three)
