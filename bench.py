@@ -68,6 +68,8 @@ def parse():
                    help="after the timed steps, run vest_autosearch (Algorithm 2, VeST_auto) for up to this many "
                         "iterations from the initial model and report it")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--accuracy-sweeps", type=int, default=20,
+                   help="sweeps of the FP32-against-FP64 GPU comparison after the timed region (0: skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     return p.parse_args()
@@ -222,6 +224,59 @@ def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
 def whole_job_rate(world: int, units_per_step: int, steps: int, ms: float) -> float:
     """Units all ranks processed per second (each rank runs its own replica of the workload)."""
     return world * units_per_step * steps / (ms / 1e3)
+
+
+def precision_gap(w: datagen.Workload, sweeps: int, data=None) -> dict:
+    """The FP32 path against the FP64 GPU path on the same data and from the same start.
+
+    The tensor values and the initial model are the FP32 numbers of the workload, cast up for the
+    FP64 run, so both runs start from identical values.  Each sweep is the factor sweep over every
+    mode followed by the core sweep (no pruning); the objective (Eq. 1 / Eq. 2) and RE (Eq. 4) are
+    taken after every sweep.  Returns the per-sweep relative objective gap |f32 - f64| / f64, the
+    RE gap, the largest relative factor and core differences after the last sweep, and the FP64
+    objective's relative change over the last sweep (how far from convergence the comparison is)."""
+    import torch
+
+    from paper_1904_02603_gb300 import vest as V
+    t, st = data if data is not None else datagen.make(w, device="cuda")[:2]
+    reg = V.REG_LF if w.reg == "LF" else V.REG_L1
+    idx = torch.from_numpy(np.ascontiguousarray(t.idx)).cuda()
+    v32 = torch.from_numpy(np.ascontiguousarray(t.val.astype(np.float32))).cuda()
+    st32 = st.astype(np.float32)
+    runs = {}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        ix = V.vest_build_index(V.Tensor(t.dims, idx, v32.to(dt)))
+        m = V.Model.from_host(st32, dtype=dt)
+        sc = V.make_scratch(ix, m)
+        losses = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(sweeps):
+            V.vest_sweep_factors(ix, m, reg, w.lam, -1, sc)
+            V.vest_sweep_core(ix, m, reg, w.lam, sc)
+            losses.append(V.vest_loss(ix, m, reg, w.lam, sc))
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        f, c, _, _ = m.to_host()
+        runs[name] = {"loss": torch.stack(losses).cpu().numpy(), "factors": f, "core": c, "s_per_sweep": sec / sweeps}
+        del ix, m, sc
+        torch.cuda.empty_cache()
+    o32, o64 = runs["f32"]["loss"][:, 3], runs["f64"]["loss"][:, 3]
+    r32, r64 = runs["f32"]["loss"][:, 4], runs["f64"]["loss"][:, 4]
+
+    def rel(a, b):
+        a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+        return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+    gap = np.abs(o32 - o64) / np.abs(o64)
+    return {"workload": w.name, "sweeps": sweeps, "reg": w.reg, "lambda": w.lam,
+            "rel_obj_gap": gap.tolist(), "final_rel_obj_gap": float(gap[-1]), "max_rel_obj_gap": float(gap.max()),
+            "re_gap": (np.abs(r32 - r64) / np.abs(r64)).tolist(),
+            "obj_f64": o64.tolist(), "re_f64": r64.tolist(),
+            "f64_last_sweep_rel_change": float(abs(o64[-1] - o64[-2]) / o64[-2]) if sweeps > 1 else None,
+            "factor_rel_gap": max(rel(a, b) for a, b in zip(runs["f32"]["factors"], runs["f64"]["factors"])),
+            "core_rel_gap": rel(runs["f32"]["core"], runs["f64"]["core"]),
+            "s_per_sweep": {"f32": runs["f32"]["s_per_sweep"], "f64": runs["f64"]["s_per_sweep"]}}
 
 
 def profiled_traffic(workload: str):
@@ -736,6 +791,11 @@ def main():
     e2e_ms = max_over_ranks(e2e_ms, world)
     e2e_value = whole_job_rate(world, units_per_step, args.e2e_steps, e2e_ms) if args.e2e_steps > 0 else None
 
+    # ---------------- the FP32 path against the FP64 GPU path (after the timed region)
+    accuracy = None
+    if w.dtype == "f32" and args.accuracy_sweeps > 0 and rank == 0:
+        accuracy = precision_gap(w, args.accuracy_sweeps, (t, st))
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -793,6 +853,7 @@ def main():
         "final_loss": {"sq_err": final_loss[0], "objective": final_loss[3], "re": final_loss[4]},
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "accuracy": accuracy,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": args.e2e_steps, "includes": "H2D of idx+val, vest_build_index, one step, D2H of the loss"},
         "clocks": clk,

@@ -146,6 +146,15 @@ const char* vest_last_error(void);
  * threads, all devices): a diagnostic for profiling and launch budgets. */
 uint64_t vest_launch_count(void);
 
+/* Device-side status.  Kernels never trap: a wait with a bounded number of polls
+ * that runs out (the tensor-core completion wait of the FP32 factor sweep, which
+ * a healthy GPU never exhausts) abandons the rest of its work, raises a bit
+ * here and returns, and the results of that call are not valid.  This call
+ * synchronises the device, writes the bits raised since the last clear to
+ * *flags (nullable; bit 0: a factor-sweep wait gave up), clears them when
+ * clear != 0, and returns VEST_ERR_TIMEOUT when any was set, else VEST_OK. */
+vest_status vest_device_status(uint32_t* flags, int32_t clear);
+
 /* ---- a1: mode-n index (the sets Omega^(n)_{i_n} of the symbol table, used by
  * Algorithm 3 and Algorithm 4).  For every mode n the observed entries are
  * stably sorted by i_n (ties keep COO order) with a device radix sort; the
@@ -279,8 +288,11 @@ vest_status vest_iteration(const vest_index* ix, vest_model* m, int32_t reg, dou
  *     in the model dtype) plus about 12 KB of partial sums must fit in 1 MiB;
  *     larger models get VEST_ERR_WORKSPACE and should use vest_loss().
  *   - The first call on a device looks up the array's device address (one
- *     cudaGetSymbolAddress with that device current) and caches it; make that
- *     first call before any stream capture.
+ *     cudaGetSymbolAddress with that device current) and keeps it for that
+ *     device's CUDA context; make that first call before any stream capture.
+ *     If the context is replaced (cudaDeviceReset, then new work), the next
+ *     call sees the new context and looks the address up again.
+ *   - Input checks are those of vest_loss(): both accept the same inputs.
  *   - Every call on a device shares the one array and overwrites what the
  *     previous call left there (nothing in it needs to start at zero: each
  *     call writes every value it reads).  Calls that overlap on the GPU race

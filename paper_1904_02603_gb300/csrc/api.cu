@@ -60,7 +60,7 @@ static vest_status check_model(const vest_model* m) {
   return VEST_OK;
 }
 
-static vest_status check_pair(const vest_index* ix, const vest_model* m) {
+vest_status check_pair(const vest_index* ix, const vest_model* m) {
   if (!ix) return fail(VEST_ERR_INVALID, "index is NULL");
   VEST_TRY(check_model(m));
   if (ix->order != m->order) return fail(VEST_ERR_INVALID, "index and model order differ");
@@ -156,7 +156,15 @@ using namespace vest;
 
 extern "C" {
 
-const char* vest_version(void) { return "vest-gb300 0.1 (sm_103a)"; }
+const char* vest_version(void) { return "vest-gb300 0.2 (sm_103a)"; }
+
+vest_status vest_device_status(uint32_t* flags, int32_t clear) {
+  uint32_t f = 0;
+  VEST_TRY(sweep_device_status(&f, clear != 0));
+  if (flags) *flags = f;
+  if (f) return fail(VEST_ERR_TIMEOUT, "a bounded device wait gave up since the last clear (flags " + std::to_string(f) + ")");
+  return VEST_OK;
+}
 const char* vest_last_error(void) { return g_last_error.c_str(); }
 uint64_t vest_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 

@@ -22,8 +22,10 @@
 // instead of one lane per row inside the task kernel.  Rows of A^(n) are
 // independent (delta does not involve A^(n)), so the order is free.
 #include <algorithm>
+#include <cstdlib>
 
 #include "delta.cuh"
+#include "tcgen05.cuh"
 
 namespace vest {
 
@@ -144,6 +146,101 @@ __device__ inline void sweep_tile(int t, int JN, int Jn, int mode, int2& cab, in
   out = make_int4(o[0], o[1], o[2], o[3]);
 }
 
+// Shared memory of a task after the kernel's own leading region (`off` bytes): row starts,
+// staged vectors V, per-piece sums, long-piece partials, tile table, carried row sums.
+template <typename T>
+struct TaskSmem {
+  int64_t* sptr;
+  T* sV;
+  T* sAcc;
+  T* sPart;
+  int4* sOut;
+  int2* sCab;
+  T* sCarry;
+};
+
+template <typename T>
+__device__ __forceinline__ TaskSmem<T> carve_task_smem(unsigned char* base, size_t off, int TASK, int L, int KMAX, int P,
+                                                       int NT) {
+  TaskSmem<T> t;
+  off = (off + 15) & ~(size_t)15;
+  t.sptr = reinterpret_cast<int64_t*>(base + off);
+  off += (size_t)(TASK + 2) * 8;
+  off = (off + 15) & ~(size_t)15;
+  t.sV = reinterpret_cast<T*>(base + off);
+  off += (size_t)TASK * L * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  t.sAcc = reinterpret_cast<T*>(base + off);
+  off += (size_t)KMAX * P * sizeof(T);
+  t.sPart = reinterpret_cast<T*>(base + off);
+  off += (size_t)long_chunks(TASK) * NT * 4 * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  t.sOut = reinterpret_cast<int4*>(base + off);
+  off += (size_t)NT * sizeof(int4);
+  t.sCab = reinterpret_cast<int2*>(base + off);
+  off += (size_t)NT * sizeof(int2);
+  off = (off + 15) & ~(size_t)15;
+  t.sCarry = reinterpret_cast<T*>(base + off);
+  return t;
+}
+
+// Phases 2 and 3 of one task, after its staged vectors V are in shared memory: per-row sums
+// over the task's row pieces, then store, carry or spill them (see the top of this file).
+template <typename T, int MODE>
+__device__ __forceinline__ void task_row_sums(const SweepArgs& a, int JN, int64_t task, int64_t tb, int64_t te,
+                                              int64_t t0, int64_t t1, int nrows, int64_t k0, const int64_t* sptr,
+                                              int NT, const int2* sCab, const int4* sOut, const T* sV, T* sAcc,
+                                              T* sPart, PieceScratch* pscr, T* cin, T* cout) {
+  const int KMAX = a.kmax, P = a.P, TASK = a.task;
+  const int L = JN + 2;
+  const int64_t rt0 = tb * TASK;
+  for (int r0 = 0; r0 < nrows; r0 += KMAX) {
+    const int nr = min(KMAX, nrows - r0);
+    // phase 2: per-row sums over the task's pieces r0 .. r0 + nr - 1
+    piece_sums<T, MODE == kModeResp>(sptr + r0, nr, t0, t1, NT, P, sCab, sOut, sV, L, JN, sAcc, sPart, pscr);
+    // phase 3: store the sums of rows that end here; carry a row that continues into
+    // the block's next task; spill rows cut by the edges of the block's task range
+    for (int kr = threadIdx.x; kr < nr; kr += blockDim.x) {
+      const int k = r0 + kr;
+      const int64_t rs = sptr[k], re = sptr[k + 1];
+      const T* piece = sAcc + kr * P;
+      const bool carried_in = (k == 0) && rs < t0 && task > tb;  // earlier pieces are in cin
+      const bool continues = re > t1;
+      const bool started_here = rs >= rt0;
+      if (!continues && !carried_in && rs >= t0) {
+        T* dst = a.rowbuf_t<T>() + (size_t)(k0 + k) * P;
+        for (int i = 0; i < P; ++i) dst[i] = piece[i];
+      } else {
+        // running sums of a row cut by task edges: (sum, compensation) in T
+        T* as = continues ? cout : cin;
+        T* ac = as + P;
+        for (int i = 0; i < P; ++i) {
+          T sum = carried_in ? cin[i] : T(0), cmp = carried_in ? cin[P + i] : T(0);
+          const T y = piece[i] - cmp;
+          const T t = sum + y;
+          ac[i] = (t - sum) - y;
+          as[i] = t;
+        }
+        if (!continues) {
+          if (started_here) {
+            T* dst = a.rowbuf_t<T>() + (size_t)(k0 + k) * P;
+            for (int i = 0; i < P; ++i) dst[i] = as[i] - ac[i];
+          } else {  // the row entered the block's range from an earlier block: incoming partial
+            double* sp = a.spill + ((size_t)blockIdx.x * 2 + 0) * P;
+            for (int i = 0; i < P; ++i) sp[i] = (double)as[i] - (double)ac[i];
+          }
+        } else if (task + 1 == te) {  // leaves the block's range
+          double* sp = a.spill + ((size_t)blockIdx.x * 2 + (started_here ? 1 : 0)) * P;
+          for (int i = 0; i < P; ++i) sp[i] = (double)as[i] - (double)ac[i];
+          a.spanning[blockIdx.x] = started_here ? (int32_t)(k0 + k) : -1;
+        }
+      }
+      if (k == nrows - 1 && task + 1 == te && !(continues && started_here)) a.spanning[blockIdx.x] = -1;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T, int JN, int JF, int NSLOW, int MODE, int E>
 __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 / E))) sweep_task_kernel(DevModel<T> M, DevMode<T> csr, const T* __restrict__ gcore,
                                                          SweepArgs a) {
@@ -154,27 +251,15 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
   const int P = a.P;
   const int NT = sweep_tiles(JN, MODE);
   const int64_t core_elems = r.n_outer * r.Jf * JN;
-  // shared layout: core | sptr | V | acc | long-piece partials | tile table
+  // shared layout: core | sptr | V | acc | long-piece partials | tile table | carry
   T* sG = reinterpret_cast<T*>(smem_raw);
-  size_t off = a.use_smem_core ? (size_t)core_elems * sizeof(T) : 0;
-  off = (off + 15) & ~(size_t)15;
-  int64_t* sptr = reinterpret_cast<int64_t*>(smem_raw + off);
-  off += (size_t)(TASK + 2) * 8;
-  off = (off + 15) & ~(size_t)15;
-  T* sV = reinterpret_cast<T*>(smem_raw + off);
-  off += (size_t)TASK * L * sizeof(T);
-  off = (off + 15) & ~(size_t)15;
-  T* sAcc = reinterpret_cast<T*>(smem_raw + off);
-  off += (size_t)KMAX * P * sizeof(T);
-  T* sPart = reinterpret_cast<T*>(smem_raw + off);
-  off += (size_t)long_chunks(TASK) * NT * 4 * sizeof(T);
-  off = (off + 15) & ~(size_t)15;
-  int4* sOut = reinterpret_cast<int4*>(smem_raw + off);
-  off += (size_t)NT * sizeof(int4);
-  int2* sCab = reinterpret_cast<int2*>(smem_raw + off);
-  off += (size_t)NT * sizeof(int2);
-  off = (off + 15) & ~(size_t)15;
-  T* sCarry = reinterpret_cast<T*>(smem_raw + off);  // [2][sum, compensation][P]: row sums carried to the next task
+  const TaskSmem<T> ts = carve_task_smem<T>(smem_raw, a.use_smem_core ? (size_t)core_elems * sizeof(T) : 0, TASK,
+                                            L, KMAX, P, NT);
+  int64_t* sptr = ts.sptr;
+  T* sV = ts.sV;
+  int4* sOut = ts.sOut;
+  int2* sCab = ts.sCab;
+  T* sCarry = ts.sCarry;  // [2][sum, compensation][P]: row sums carried to the next task
   __shared__ PieceScratch pscr;
 
   const T* g = gcore;
@@ -187,9 +272,8 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
   const int64_t nnz = csr.nnz;
   __syncthreads();
 
-  // this block's consecutive tasks [tb, te) and the positions [rt0, rt1) they cover
+  // this block's consecutive tasks [tb, te)
   const int64_t tb = blockIdx.x * a.tpc, te = min(tb + a.tpc, a.ntasks);
-  const int64_t rt0 = tb * TASK;
   for (int64_t task = tb; task < te; ++task) {
     const int64_t t0 = task * TASK, t1 = min(t0 + (int64_t)TASK, nnz);
     const int cnt = (int)(t1 - t0);
@@ -225,52 +309,242 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
     }
     __syncthreads();
 
-    for (int r0 = 0; r0 < nrows; r0 += KMAX) {
-      const int nr = min(KMAX, nrows - r0);
-      // phase 2: per-row sums over the task's pieces r0 .. r0 + nr - 1
-      piece_sums<T, MODE == kModeResp>(sptr + r0, nr, t0, t1, NT, P, sCab, sOut, sV, L, JN, sAcc, sPart, &pscr);
-      // phase 3: store the sums of rows that end here; carry a row that continues into
-      // the block's next task; spill rows cut by the edges of the block's task range
-      for (int kr = threadIdx.x; kr < nr; kr += blockDim.x) {
-        const int k = r0 + kr;
-        const int64_t rs = sptr[k], re = sptr[k + 1];
-        const T* piece = sAcc + kr * P;
-        const bool carried_in = (k == 0) && rs < t0 && task > tb;  // earlier pieces are in cin
-        const bool continues = re > t1;
-        const bool started_here = rs >= rt0;
-        if (!continues && !carried_in && rs >= t0) {
-          T* dst = a.rowbuf_t<T>() + (size_t)(k0 + k) * P;
-          for (int i = 0; i < P; ++i) dst[i] = piece[i];
-        } else {
-          // running sums of a row cut by task edges: (sum, compensation) in T
-          T* as = continues ? cout : cin;
-          T* ac = as + P;
-          for (int i = 0; i < P; ++i) {
-            T sum = carried_in ? cin[i] : T(0), cmp = carried_in ? cin[P + i] : T(0);
-            const T y = piece[i] - cmp;
-            const T t = sum + y;
-            ac[i] = (t - sum) - y;
-            as[i] = t;
-          }
-          if (!continues) {
-            if (started_here) {
-              T* dst = a.rowbuf_t<T>() + (size_t)(k0 + k) * P;
-              for (int i = 0; i < P; ++i) dst[i] = as[i] - ac[i];
-            } else {  // the row entered the block's range from an earlier block: incoming partial
-              double* sp = a.spill + ((size_t)blockIdx.x * 2 + 0) * P;
-              for (int i = 0; i < P; ++i) sp[i] = (double)as[i] - (double)ac[i];
-            }
-          } else if (task + 1 == te) {  // leaves the block's range
-            double* sp = a.spill + ((size_t)blockIdx.x * 2 + (started_here ? 1 : 0)) * P;
-            for (int i = 0; i < P; ++i) sp[i] = (double)as[i] - (double)ac[i];
-            a.spanning[blockIdx.x] = started_here ? (int32_t)(k0 + k) : -1;
-          }
-        }
-        if (k == nrows - 1 && task + 1 == te && !(continues && started_here)) a.spanning[blockIdx.x] = -1;
-      }
-      __syncthreads();
+    task_row_sums<T, MODE>(a, JN, task, tb, te, t0, t1, nrows, k0, sptr, NT, sCab, sOut, sV, ts.sAcc, ts.sPart, &pscr,
+                           cin, cout);
+  }
+}
+
+// ------------------------------------------------------------------ tensor-core delta (FP32)
+// Eq. 11 in two stages for each group of 128 entries (one entry per TMEM lane):
+//   stage 1, tcgen05 MMA in split TF32 (hi*hi + hi*lo + lo*hi, about FP32 accuracy):
+//     T[e][(o, j)] = sum_k A[e][k] B[k][(o, j)], with A[e] the row of the other mode f
+//     (NA = 1) or the Khatri-Rao product of the rows of f and of the first slow mode
+//     (NA = 2), and B the core permuted to (k, (o, j_n)), o over the one remaining other
+//     mode (or a single o when none remains);
+//   stage 2, FP32 FMAs: delta_e(j) = sum_o w_e(o) T[e][(o, j)], w_e the row of the
+//     remaining mode (1 when none remains).
+// With the dense 10 x 10 x 10 core of the Zipf workload this moves 1000 of the 1100 FMAs
+// per entry of the staged contraction onto the tensor cores.  A is written to TMEM from
+// registers by its own lane, B sits in shared memory (K-major, no swizzle), the
+// accumulator in TMEM; one thread issues the MMAs and commits them to an mbarrier that
+// every thread waits on with a bounded number of polls.
+struct TcPlan {
+  int na;        // other modes folded into A: 1 or 2
+  int jf8;       // rank of mode f rounded up to 8: A columns per row of the second A mode
+  int JA1;       // rank of the second A mode (1 when na = 1)
+  int Kp;        // A width: jf8 * JA1, a multiple of 8 (the MMA's K step)
+  int O;         // rows of B per j block: rank of the remaining mode (1 when none)
+  int has_rest;  // a remaining mode exists
+  int Np;        // MMA N: O * CS rounded up to 16
+  int ncols;     // TMEM columns allocated: power of two >= 2 Kp + Np
+  size_t btile;  // bytes of one B tile (hi or lo): Np * Kp * 4
+};
+
+constexpr uint32_t kTcWaitPolls = 1u << 22;  // bounded mbarrier wait (seconds at worst, never in practice)
+static __device__ unsigned int g_sweep_status;  // bit 0: an MMA completion wait gave up
+
+template <int CS>
+__device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[CS]) {
+  if constexpr (CS == 8) {
+    uint32_t u[8];
+    tc::ld8(taddr, u);
+    tc::wait_ld();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(u[i]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < CS; c += 16) {
+      uint32_t u[16];
+      tc::ld16(taddr + c, u);
+      tc::wait_ld();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[c + i] = __uint_as_float(u[i]);
     }
   }
+}
+
+template <int JN, int MODE, int NA>
+__global__ void __launch_bounds__(128, 2) sweep_task_tc_kernel(DevModel<float> M, DevMode<float> csr,
+                                                               const float* __restrict__ gp, SweepArgs a, TcPlan tp) {
+  using T = float;
+  constexpr int E = 2;  // entries per thread: two groups of 128
+  constexpr int CS = JN <= 8 ? 8 : (JN <= 16 ? 16 : 32);
+  constexpr int L = JN + 2;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t mma_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ PieceScratch pscr;
+  const ModeRoles& r = a.r;
+  const int TASK = a.task, KMAX = a.kmax, P = a.P;
+  const int NT = sweep_tiles(JN, MODE);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // shared layout: B hi | B lo | sptr | V | acc | long-piece partials | tile table | carry
+  uint32_t* sBhi = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* sBlo = reinterpret_cast<uint32_t*>(smem_raw + tp.btile);
+  const TaskSmem<T> ts = carve_task_smem<T>(smem_raw, 2 * tp.btile, TASK, L, KMAX, P, NT);
+
+  // B tiles from the permuted core gp[((o_full * Jf + cf) * JN + j]: element (n, k) with
+  // n = o * CS + j, k = s0 * jf8 + cf (s0 = 0 when na = 1), o_full = o (na = 1) or s0 + JA1 o
+  for (int e = tid; e < tp.Np * tp.Kp; e += blockDim.x) {
+    const int n = e / tp.Kp, k = e - n * tp.Kp;
+    const int o = n / CS, j = n - o * CS;
+    const int s0 = NA == 2 ? k / tp.jf8 : 0, cf = NA == 2 ? k - s0 * tp.jf8 : k;
+    float v = 0.f;
+    if (j < r.Jn && cf < r.Jf && o < tp.O && s0 < tp.JA1) {
+      const int64_t of = NA == 2 ? (int64_t)s0 + (int64_t)tp.JA1 * o : (int64_t)o;
+      v = gp[(of * r.Jf + cf) * JN + j];
+    }
+    uint32_t hi, lo;
+    tc::split_tf32(v, hi, lo);
+    const uint32_t w = tc::kmajor_offset(n, k, tp.Kp) >> 2;
+    sBhi[w] = hi;
+    sBlo[w] = lo;
+  }
+  for (int t = tid; t < NT; t += blockDim.x) sweep_tile(t, JN, r.Jn, MODE, ts.sCab[t], ts.sOut[t]);
+  if (tid == 0) tc::mbar_init(&mma_bar, 1);
+  if (warp == 0) tc::tmem_alloc(&tmem_slot, (uint32_t)tp.ncols);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = tmem_slot;
+  const uint32_t lane = (uint32_t)(32 * (warp & 3)) << 16;
+  const uint32_t colA = 0, colAlo = (uint32_t)tp.Kp, colD = 2u * (uint32_t)tp.Kp;
+  const uint32_t idesc = tc::idesc_tf32(128, tp.Np);
+  const uint32_t sbo = (uint32_t)tp.Kp * 32u;
+  const uint32_t bhi_addr = tc::smem_u32(sBhi), blo_addr = tc::smem_u32(sBlo);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  const int R = *csr.nnzrows;
+  const int64_t nnz = csr.nnz;
+  const int64_t tb = blockIdx.x * a.tpc, te = min(tb + a.tpc, a.ntasks);
+  for (int64_t task = tb; task < te && !failed; ++task) {
+    const int64_t t0 = task * TASK, t1 = min(t0 + (int64_t)TASK, nnz);
+    const int cnt = (int)(t1 - t0);
+    int64_t k0;
+    const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, ts.sptr, &k0);
+    T* cin = ts.sCarry + (task & 1) * 2 * P;
+    T* cout = ts.sCarry + ((task + 1) & 1) * 2 * P;
+
+    // gathers for both entries of the thread: rows of the A modes, the remaining mode's row, X (or r)
+    float a0[E][16], a1[E][NA == 2 ? 16 : 1], wr[E][16], xv[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int q = tid + e * 128;
+      const bool valid = q < cnt;
+      const int64_t p = t0 + (valid ? q : 0);
+      const float* ra0 = M.A[r.f] + (int64_t)csr.oidx[p] * r.Jf;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) a0[e][i] = (valid && i < r.Jf) ? __ldg(ra0 + i) : 0.f;
+      if constexpr (NA == 2) {
+        const float* ra1 = M.A[r.slow[0]] + (int64_t)csr.oidx[nnz + p] * tp.JA1;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) a1[e][i] = (valid && i < tp.JA1) ? __ldg(ra1 + i) : 0.f;
+      }
+      if (tp.has_rest) {
+        const float* rr = M.A[r.slow[NA - 1]] + (int64_t)csr.oidx[(int64_t)NA * nnz + p] * tp.O;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) wr[e][i] = (valid && i < tp.O) ? __ldg(rr + i) : 0.f;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) wr[e][i] = i == 0 ? 1.f : 0.f;
+      }
+      if constexpr (MODE == kModeUpdate) xv[e] = valid ? csr.val[p] : 0.f;
+      else xv[e] = valid ? static_cast<const T*>(a.resid_coo)[csr.perm[p]] : 0.f;
+    }
+
+#pragma unroll
+    for (int g = 0; g < E; ++g) {
+      // A operand of this lane: hi at columns [0, Kp), lo at [Kp, 2 Kp)
+      if constexpr (NA == 1) {
+#pragma unroll
+        for (int c = 0; c < 16; c += 8) {
+          if (c < tp.Kp) {
+            uint32_t h[8], l[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) tc::split_tf32(a0[g][c + i], h[i], l[i]);
+            tc::st8(tbase + lane + colA + c, h);
+            tc::st8(tbase + lane + colAlo + c, l);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int s0 = 0; s0 < 16; ++s0) {
+          if (s0 < tp.JA1) {
+            const float w0 = a1[g][s0];
+#pragma unroll
+            for (int c = 0; c < 16; c += 8) {
+              if (c < tp.jf8) {
+                uint32_t h[8], l[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) tc::split_tf32(a0[g][c + i] * w0, h[i], l[i]);
+                const uint32_t col = (uint32_t)(s0 * tp.jf8 + c);
+                tc::st8(tbase + lane + colA + col, h);
+                tc::st8(tbase + lane + colAlo + col, l);
+              }
+            }
+          }
+        }
+      }
+      tc::wait_st();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+        for (int ks = 0; ks < tp.Kp / 8; ++ks) {
+          const uint64_t bh = tc::smem_desc(bhi_addr + (uint32_t)ks * 256u, 128u, sbo);
+          const uint64_t bl = tc::smem_desc(blo_addr + (uint32_t)ks * 256u, 128u, sbo);
+          tc::mma_tf32_ts(tbase + colD, tbase + colA + ks * 8, bh, idesc, ks > 0 ? 1u : 0u);
+          tc::mma_tf32_ts(tbase + colD, tbase + colA + ks * 8, bl, idesc, 1u);
+          tc::mma_tf32_ts(tbase + colD, tbase + colAlo + ks * 8, bh, idesc, 1u);
+        }
+        tc::mma_commit(&mma_bar);
+      }
+      __syncwarp();
+      const bool done = tc::mbar_wait_bounded(&mma_bar, phase, kTcWaitPolls);
+      if (__syncthreads_or(!done)) {
+        failed = true;
+        break;
+      }
+      phase ^= 1u;
+      tc::fence_after_sync();
+      // stage 2: delta(j) = sum_o w(o) T[(o, j)]
+      float d[JN];
+#pragma unroll
+      for (int j = 0; j < JN; ++j) d[j] = 0.f;
+#pragma unroll
+      for (int o = 0; o < 16; ++o) {
+        if (o < tp.O) {
+          float v[CS];
+          tmem_load_cols<CS>(tbase + lane + colD + (uint32_t)(o * CS), v);
+#pragma unroll
+          for (int j = 0; j < JN; ++j) d[j] = fmaf(wr[g][o], v[j], d[j]);
+        }
+      }
+      const int q = tid + g * 128;
+      if (q < cnt) {
+        T* dst = ts.sV + q * L;
+#pragma unroll
+        for (int j = 0; j < JN; ++j) dst[j] = d[j];
+        dst[JN] = xv[g];
+        dst[JN + 1] = T(0);
+      }
+      tc::fence_before_sync();  // this group's TMEM reads before the next group's MMAs
+    }
+    if (failed) break;
+    __syncthreads();
+    task_row_sums<T, MODE>(a, JN, task, tb, te, t0, t1, nrows, k0, ts.sptr, NT, ts.sCab, ts.sOut, ts.sV, ts.sAcc,
+                           ts.sPart, &pscr, cin, cout);
+  }
+  if (failed) {
+    // the MMAs may still be in flight: give them another bounded wait before TMEM is freed
+    if (tid == 0) atomicOr(&g_sweep_status, 1u);
+    tc::mbar_wait_bounded(&mma_bar, phase, kTcWaitPolls);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, (uint32_t)tp.ncols);
 }
 
 // Rows cut by the edges of the blocks' task ranges: the block where the row starts
@@ -431,6 +705,84 @@ static vest_status dispatch_jn(int JN, int nslow, int Jf, const DevModel<T>& M, 
   }
 }
 
+// ------------------------------------------------------------------ tensor-core path selection
+// The tensor-core delta serves FP32 models whose other modes split into one or two A modes
+// (ranks <= 16) and at most one remaining mode (rank <= 16), with 2 Kp + Np <= 256 TMEM
+// columns.  Among the feasible splits the one with the least CUDA-core work per entry is
+// taken: stage 2's O * JN FMAs plus the A split (and, with two A modes, their products).
+// VEST_TENSOR_CORES=0 in the environment selects the FMA kernels everywhere.
+static bool tensor_cores_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("VEST_TENSOR_CORES");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+static bool tc_plan(const ModeRoles& r, int order, int JN, TcPlan* out) {
+  if (!tensor_cores_enabled()) return false;
+  const int CS = JN <= 8 ? 8 : (JN <= 16 ? 16 : 32);
+  int best = 1 << 30;
+  bool found = false;
+  for (int na = 1; na <= 2; ++na) {
+    const int nother = order - 1;
+    if (na > nother) break;
+    const int nrest = nother - na;
+    if (nrest > 1) continue;
+    const int ja1 = na == 2 ? r.Js[0] : 1;
+    const int jr = nrest ? r.Js[na - 1] : 1;
+    if (r.Jf > 16 || ja1 > 16 || jr > 16) continue;
+    TcPlan p{};
+    p.na = na;
+    p.jf8 = (r.Jf + 7) / 8 * 8;
+    p.JA1 = ja1;
+    p.Kp = p.jf8 * ja1;
+    p.O = jr;
+    p.has_rest = nrest;
+    p.Np = (jr * CS + 15) / 16 * 16;
+    if (2 * p.Kp + p.Np > 256) continue;
+    p.ncols = 32;
+    while (p.ncols < 2 * p.Kp + p.Np) p.ncols *= 2;
+    p.btile = (size_t)p.Np * p.Kp * 4;
+    const int cost = jr * JN + (na == 2 ? 3 : 2) * p.Kp;
+    if (cost < best) {
+      best = cost;
+      *out = p;
+      found = true;
+    }
+  }
+  return found;
+}
+
+template <int JN, int MODE>
+static vest_status launch_tc(const DevModel<float>& M, const DevMode<float>& csr, const float* gp, const SweepArgs& a,
+                             const TcPlan& tp, cudaStream_t s) {
+  size_t smem = task_smem<float>(a.task, a.kmax, JN, a.P, MODE, 2 * tp.btile);
+  // no more CTAs on an SM than its 512 TMEM columns hold, so no allocation ever waits
+  const int per_sm = 512 / tp.ncols;
+  const size_t sm_bytes = 228 * 1024, reserved = 1024;
+  smem = std::max(smem, sm_bytes / (per_sm + 1) - reserved + 16);
+  if (smem > kSmemMax) return fail(VEST_ERR_UNSUPPORTED, "tensor-core factor sweep: shared memory exceeds 227 KB");
+  auto kern = tp.na == 2 ? sweep_task_tc_kernel<JN, MODE, 2> : sweep_task_tc_kernel<JN, MODE, 1>;
+  VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)ceil_div(a.ntasks, a.tpc), 128, smem, s>>>(M, csr, gp, a, tp);
+  VEST_LAUNCH("sweep_task_tc_kernel");
+  return VEST_OK;
+}
+
+template <int MODE>
+static vest_status dispatch_tc(int JN, const DevModel<float>& M, const DevMode<float>& csr, const float* gp,
+                               const SweepArgs& a, const TcPlan& tp, cudaStream_t s) {
+  switch (JN) {
+    case 4: return launch_tc<4, MODE>(M, csr, gp, a, tp, s);
+    case 8: return launch_tc<8, MODE>(M, csr, gp, a, tp, s);
+    case 10: return launch_tc<10, MODE>(M, csr, gp, a, tp, s);
+    case 12: return launch_tc<12, MODE>(M, csr, gp, a, tp, s);
+    case 16: return launch_tc<16, MODE>(M, csr, gp, a, tp, s);
+    default: return launch_tc<32, MODE>(M, csr, gp, a, tp, s);
+  }
+}
+
 template <typename T, int MODE>
 static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, SweepArgs a, char* scratch,
                             const ScratchPlan& plan, cudaStream_t s) {
@@ -472,7 +824,16 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
     smem = task_smem<T>(a.task, a.kmax, JN, a.P, MODE, use_smem ? (size_t)core_elems * sizeof(T) : 0);
   }
   if (smem > kSmemMax) return fail(VEST_ERR_UNSUPPORTED, "factor sweep: shared memory of one task exceeds 227 KB");
-  VEST_TRY(dispatch_jn<T, MODE>(JN, r.nslow, r.Jf, M, csr, gp, a, smem, s));
+  TcPlan tp{};
+  if constexpr (sizeof(T) == 4) {
+    if (a.task == 256 && tc_plan(r, M.N, JN, &tp)) {
+      VEST_TRY(dispatch_tc<MODE>(JN, M, csr, gp, a, tp, s));
+    } else {
+      VEST_TRY(dispatch_jn<T, MODE>(JN, r.nslow, r.Jf, M, csr, gp, a, smem, s));
+    }
+  } else {
+    VEST_TRY(dispatch_jn<T, MODE>(JN, r.nslow, r.Jf, M, csr, gp, a, smem, s));
+  }
   const size_t fsmem = (size_t)std::max(1, 256 / a.P) * a.P * 8 + 8 * a.P;
   auto fk = sweep_fixup_kernel<T, MODE>;
   VEST_CUDA(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
@@ -508,6 +869,20 @@ vest_status responsibility_factors(const vest_index* ix, const vest_model* m, co
     a.resp = resp_factor ? resp_factor[n] : nullptr;
     VEST_TRY((run_mode<T, kModeResp>(ix, M, n, a, scratch, plan, s)));
   }
+  return VEST_OK;
+}
+
+// Bits set by the factor-sweep kernels since the last clear (bit 0: a bounded wait on the
+// tensor cores gave up); synchronises the device to read them.
+vest_status sweep_device_status(uint32_t* flags, bool clear) {
+  VEST_CUDA(cudaDeviceSynchronize());
+  unsigned int v = 0;
+  VEST_CUDA(cudaMemcpyFromSymbol(&v, g_sweep_status, sizeof(v)));
+  if (clear && v) {
+    const unsigned int z = 0;
+    VEST_CUDA(cudaMemcpyToSymbol(g_sweep_status, &z, sizeof(z)));
+  }
+  *flags = v;
   return VEST_OK;
 }
 

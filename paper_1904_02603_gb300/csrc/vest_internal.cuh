@@ -152,6 +152,10 @@ inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 int num_sms();
 
+// Argument checks shared by every entry point that takes an index and a model:
+// order, dtype, ranks, dims, pointers and the size limits of the library.
+vest_status check_pair(const vest_index* ix, const vest_model* m);
+
 // Generic device scans (exclusive) used by the index build and the prune.
 vest_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, cudaStream_t s);
 vest_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s);
@@ -162,6 +166,10 @@ template <typename K>
 vest_status radix_sort_pairs(K* keys, int32_t* vals, K* keys_alt, int32_t* vals_alt, int64_t n, int bits,
                              int32_t* hist, int32_t* scan_tmp, bool* result_in_alt, cudaStream_t s);
 size_t radix_hist_elems(int64_t n);
+
+// Status bits the factor-sweep kernels raise instead of trapping (bit 0: a bounded wait
+// on the tensor cores gave up); reads them after a device synchronise, clears on request.
+vest_status sweep_device_status(uint32_t* flags, bool clear);
 
 // Operations implemented in their own translation units.
 template <typename T>

@@ -226,6 +226,9 @@ WORKLOADS = {
     "zipf_2000x3_4e4": Workload("zipf_2000x3_4e4", (2000,) * 3, (10, 10, 10), 40_000, "zipf", 1.2, core_density=0.1,
                          factor_density=0.3, noise=0.01, dtype="f32", reg="LF", lam=0.01, data_seed=1011,
                          init_seed=2011),
+    "uniform_2000x4_5e6": Workload("uniform_2000x4_5e6", (2000,) * 4, (8, 8, 8, 8), 5_000_000, "uniform",
+                          core_density=0.05, factor_density=0.4, noise=0.05, dtype="f32", reg="L1", lam=0.1,
+                          data_seed=1013, init_seed=2013),
     "uniform_300x4_2e4": Workload("uniform_300x4_2e4", (300,) * 4, (8, 8, 8, 8), 20_000, "uniform", core_density=0.05,
                          factor_density=0.4, noise=0.05, dtype="f32", reg="L1", lam=0.1, data_seed=1012,
                          init_seed=2012),

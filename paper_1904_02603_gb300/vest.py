@@ -89,6 +89,7 @@ _SIGS = {
                                   C.c_size_t, _P]),
     "vest_reconstruct": (C.c_int, [C.POINTER(vest_model), _P, C.c_int64, _P, _P]),
     "vest_loss_noalloc": (C.c_int, [_P, C.POINTER(vest_model), C.c_int32, C.c_double, _P, _P, _P]),
+    "vest_device_status": (C.c_int, [C.POINTER(C.c_uint32), C.c_int32]),
 }
 
 _lib = None
@@ -270,6 +271,14 @@ class Index:
 # ------------------------------------------------------------------ entry points (same names as vest.h)
 def vest_version() -> str:
     return load().vest_version().decode()
+
+
+def vest_device_status(clear: bool = True) -> int:
+    """Synchronises the device and returns the status bits its kernels raised since the last
+    clear (0: none; bit 0: a bounded tensor-core wait of the factor sweep gave up)."""
+    f = C.c_uint32(0)
+    getattr(load(), "vest_device_status")(C.byref(f), int(clear))
+    return int(f.value)
 
 
 def vest_launch_count() -> int:
