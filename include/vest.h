@@ -155,6 +155,19 @@ uint64_t vest_launch_count(void);
  * clear != 0, and returns VEST_ERR_TIMEOUT when any was set, else VEST_OK. */
 vest_status vest_device_status(uint32_t* flags, int32_t clear);
 
+/* Peak-rate probes (measurement support, no counterpart in the paper): runs one
+ * self-timed probe on `stream` and writes its rate to *rate (host double):
+ *   kind 0  FP32 FMA throughput, TFLOP/s (independent FMA chains, every lane of every SM)
+ *   kind 1  FP64 FMA throughput, TFLOP/s
+ *   kind 2  tcgen05 TF32 MMA throughput with A in tensor memory, TFLOP/s (M = 128, N = 256,
+ *           K = 8, the operand placement of the FP32 factor sweep)
+ *   kind 3  L2 random-gather throughput of 16-byte reads, TB/s, from a table of up to
+ *           32 MiB kept in `buffer` (device, at least 4 MiB, contents overwritten)
+ * Each probe runs twice and the second run is timed with CUDA events; the call
+ * synchronises on its last event.  Clocks are left as they are: compare a rate
+ * with the SM clock seen while it ran. */
+vest_status vest_probe_peak(int32_t kind, double* rate, void* buffer, size_t buffer_bytes, void* stream);
+
 /* ---- a1: mode-n index (the sets Omega^(n)_{i_n} of the symbol table, used by
  * Algorithm 3 and Algorithm 4).  For every mode n the observed entries are
  * stably sorted by i_n (ties keep COO order) with a device radix sort; the
@@ -171,6 +184,12 @@ vest_status vest_index_mode(const vest_index* ix, int32_t mode, vest_mode_view* 
 
 /* Scratch needed by the compute calls below for this index and model shape. */
 size_t vest_scratch_bytes(const vest_index* ix, const vest_model* m);
+/* The same figure from the tensor's description alone (no index needed yet), for callers
+ * that budget device memory before building anything: equals vest_scratch_bytes() for
+ * the index vest_build_index(t) makes.  Only the shape fields of t (order, dims, nnz,
+ * val_dtype) and of m (order, dtype, dims, ranks) are read; their pointers may be
+ * NULL.  Returns 0 on invalid arguments. */
+size_t vest_scratch_bytes_for(const vest_tensor* t, const vest_model* m);
 
 /* ---- a2-a4: factor sweep (Algorithm 4; Lemma 1, Eq. 9-11 for L_F; Lemma 3,
  * Eq. 13 for L_1).  For mode n (mode >= 0) or every mode in order 0..N-1

@@ -43,7 +43,8 @@ int num_sms() {
 
 static size_t dtype_size(int dt) { return dt == VEST_F64 ? 8 : 4; }
 
-static vest_status check_model(const vest_model* m) {
+// Shape fields of a model: order, dtype, ranks, dims and the size limits.
+static vest_status check_model_shape(const vest_model* m) {
   if (!m) return fail(VEST_ERR_INVALID, "model is NULL");
   if (m->order < 2 || m->order > VEST_MAX_ORDER) return fail(VEST_ERR_INVALID, "order must be in [2, 10]");
   if (m->dtype != VEST_F64 && m->dtype != VEST_F32) return fail(VEST_ERR_INVALID, "model dtype must be F64 or F32");
@@ -51,11 +52,17 @@ static vest_status check_model(const vest_model* m) {
   for (int n = 0; n < m->order; ++n) {
     if (m->ranks[n] < 1 || m->ranks[n] > VEST_MAX_RANK) return fail(VEST_ERR_INVALID, "rank must be in [1, 32]");
     if (m->dims[n] < 1 || m->dims[n] >= (int64_t(1) << 31)) return fail(VEST_ERR_INVALID, "dims must be in [1, 2^31)");
-    if (!m->factor[n] || !m->factor_mask[n]) return fail(VEST_ERR_INVALID, "factor or mask pointer is NULL");
     if (m->dims[n] * m->ranks[n] >= (int64_t(1) << 31)) return fail(VEST_ERR_INVALID, "factor too large");
     gs *= m->ranks[n];
   }
   if (gs >= (int64_t(1) << 24)) return fail(VEST_ERR_UNSUPPORTED, "core larger than 2^24 elements");
+  return VEST_OK;
+}
+
+static vest_status check_model(const vest_model* m) {
+  VEST_TRY(check_model_shape(m));
+  for (int n = 0; n < m->order; ++n)
+    if (!m->factor[n] || !m->factor_mask[n]) return fail(VEST_ERR_INVALID, "factor or mask pointer is NULL");
   if (!m->core || !m->core_mask) return fail(VEST_ERR_INVALID, "core or core mask pointer is NULL");
   return VEST_OK;
 }
@@ -215,6 +222,24 @@ vest_status vest_index_mode(const vest_index* ix, int32_t mode, vest_mode_view* 
 size_t vest_scratch_bytes(const vest_index* ix, const vest_model* m) {
   if (check_pair(ix, m) != VEST_OK) return 0;
   return plan_scratch(ix, m).total;
+}
+
+size_t vest_scratch_bytes_for(const vest_tensor* t, const vest_model* m) {
+  // the scratch plan reads only the tensor's shape, entry count and dtype: a host-side
+  // description stands in for the index that vest_build_index would make
+  if (!t || t->order < 2 || t->order > VEST_MAX_ORDER || t->nnz < 0) return 0;
+  vest_index d{};
+  d.order = t->order;
+  d.val_dtype = t->val_dtype;
+  d.nnz = t->nnz;
+  for (int n = 0; n < t->order; ++n) {
+    d.dims[n] = t->dims[n];
+    d.mode[n].cap = std::min<int64_t>(t->dims[n], std::max<int64_t>(t->nnz, 1));
+  }
+  if (check_model_shape(m) != VEST_OK || d.order != m->order || d.val_dtype != m->dtype) return 0;
+  for (int n = 0; n < m->order; ++n)
+    if (d.dims[n] != m->dims[n]) return 0;
+  return plan_scratch(&d, m).total;
 }
 
 vest_status vest_sweep_factors(const vest_index* ix, vest_model* m, int32_t reg, double lambda, int32_t mode,

@@ -159,16 +159,22 @@ struct TaskSmem {
   T* sCarry;
 };
 
+// With v_ext set, V lives there (a region the caller shares with something else) and no
+// room is carved for it.
 template <typename T>
 __device__ __forceinline__ TaskSmem<T> carve_task_smem(unsigned char* base, size_t off, int TASK, int L, int KMAX, int P,
-                                                       int NT) {
+                                                       int NT, T* v_ext = nullptr) {
   TaskSmem<T> t;
   off = (off + 15) & ~(size_t)15;
   t.sptr = reinterpret_cast<int64_t*>(base + off);
   off += (size_t)(TASK + 2) * 8;
   off = (off + 15) & ~(size_t)15;
-  t.sV = reinterpret_cast<T*>(base + off);
-  off += (size_t)TASK * L * sizeof(T);
+  if (v_ext) {
+    t.sV = v_ext;
+  } else {
+    t.sV = reinterpret_cast<T*>(base + off);
+    off += (size_t)TASK * L * sizeof(T);
+  }
   off = (off + 15) & ~(size_t)15;
   t.sAcc = reinterpret_cast<T*>(base + off);
   off += (size_t)KMAX * P * sizeof(T);
@@ -315,7 +321,7 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
 }
 
 // ------------------------------------------------------------------ tensor-core delta (FP32)
-// Eq. 11 in two stages for each group of 128 entries (one entry per TMEM lane):
+// Eq. 11 in two stages for each group of 128 entries (one entry per accumulator row):
 //   stage 1, tcgen05 MMA in split TF32 (hi*hi + hi*lo + lo*hi, about FP32 accuracy):
 //     T[e][(o, j)] = sum_k A[e][k] B[k][(o, j)], with A[e] the row of the other mode f
 //     (NA = 1) or the Khatri-Rao product of the rows of f and of the first slow mode
@@ -324,70 +330,82 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
 //   stage 2, FP32 FMAs: delta_e(j) = sum_o w_e(o) T[e][(o, j)], w_e the row of the
 //     remaining mode (1 when none remains).
 // With the dense 10 x 10 x 10 core of the Zipf workload this moves 1000 of the 1100 FMAs
-// per entry of the staged contraction onto the tensor cores.  A is written to TMEM from
-// registers by its own lane, B sits in shared memory (K-major, no swizzle), the
-// accumulator in TMEM; one thread issues the MMAs and commits them to an mbarrier that
-// every thread waits on with a bounded number of polls.
+// per entry of the staged contraction onto the tensor cores.  B sits in shared memory
+// (K-major, no swizzle) and the accumulator in tensor memory, column o * JN + j.  With one
+// A mode, A is written to shared memory by the lane of its entry (the MMA reads both
+// operands there; the region is reused for the staged vectors V once the task's last MMA
+// has completed), so the allocation is the accumulator alone: 128 columns for the Zipf
+// workload, four CTAs per SM.  With two A modes the wider A goes to tensor memory.  One
+// thread issues the MMAs and commits them to an mbarrier that every thread waits on with a
+// bounded number of polls; a wait that runs out marks the device status and ends the CTA's
+// work after its in-flight MMAs are given the same bounded wait.
 struct TcPlan {
-  int na;        // other modes folded into A: 1 or 2
+  int na;        // other modes folded into A: 1 (A in shared memory) or 2 (A in tensor memory)
   int jf8;       // rank of mode f rounded up to 8: A columns per row of the second A mode
   int JA1;       // rank of the second A mode (1 when na = 1)
   int Kp;        // A width: jf8 * JA1, a multiple of 8 (the MMA's K step)
-  int O;         // rows of B per j block: rank of the remaining mode (1 when none)
+  int O;         // rank of the remaining mode (1 when none)
   int has_rest;  // a remaining mode exists
-  int Np;        // MMA N: O * CS rounded up to 16
-  int ncols;     // TMEM columns allocated: power of two >= 2 Kp + Np
+  int Np;        // MMA N: O * JN rounded up to 16
+  int colD;      // first accumulator column: 0 (na = 1) or 2 Kp after A hi and lo (na = 2)
+  int ncols;     // TMEM columns allocated: power of two >= colD + Np
+  int per_sm;    // CTAs per SM that the allocation allows: 512 / ncols
   size_t btile;  // bytes of one B tile (hi or lo): Np * Kp * 4
+  size_t atile;  // bytes of one A tile (hi or lo) in shared memory: 128 * Kp * 4 (0 when na = 2)
+  size_t ubytes; // shared region of A hi, A lo and, later, V: max(2 atile, V bytes), 128-aligned
 };
 
 constexpr uint32_t kTcWaitPolls = 1u << 22;  // bounded mbarrier wait (seconds at worst, never in practice)
+constexpr int kTcMaxChunks = 14;             // accumulator columns read in 16-column chunks: Np <= 224
 static __device__ unsigned int g_sweep_status;  // bit 0: an MMA completion wait gave up
 
-template <int CS>
-__device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[CS]) {
-  if constexpr (CS == 8) {
-    uint32_t u[8];
-    tc::ld8(taddr, u);
-    tc::wait_ld();
+// stage 2 for one lane: delta(j) += w(o) T[o * JN + j] over the accumulator's Np columns
+template <int JN>
+__device__ __forceinline__ void contract_rest(uint32_t taddr, int Np, int O, const float (&w)[16], float (&d)[JN]) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(u[i]);
-  } else {
-#pragma unroll
-    for (int c = 0; c < CS; c += 16) {
+  for (int c = 0; c < kTcMaxChunks * 16; c += 16) {
+    if (c < Np) {
       uint32_t u[16];
-      tc::ld16(taddr + c, u);
+      tc::ld16(taddr + (uint32_t)c, u);
       tc::wait_ld();
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[c + i] = __uint_as_float(u[i]);
+      for (int i = 0; i < 16; ++i) {
+        const int col = c + i, o = col / JN, j = col - o * JN;
+        if (o < 16 && o < O) d[j] = fmaf(w[o], __uint_as_float(u[i]), d[j]);
+      }
     }
   }
 }
 
 template <int JN, int MODE, int NA>
-__global__ void __launch_bounds__(128, 2) sweep_task_tc_kernel(DevModel<float> M, DevMode<float> csr,
-                                                               const float* __restrict__ gp, SweepArgs a, TcPlan tp) {
+__global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
+    sweep_task_tc_kernel(DevModel<float> M, DevMode<float> csr, const float* __restrict__ gp, SweepArgs a, TcPlan tp) {
   using T = float;
   constexpr int E = 2;  // entries per thread: two groups of 128
-  constexpr int CS = JN <= 8 ? 8 : (JN <= 16 ? 16 : 32);
   constexpr int L = JN + 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t mma_bar;
   __shared__ uint32_t tmem_slot;
+  __shared__ int wait_failed;
   __shared__ PieceScratch pscr;
   const ModeRoles& r = a.r;
   const int TASK = a.task, KMAX = a.kmax, P = a.P;
   const int NT = sweep_tiles(JN, MODE);
   const int tid = threadIdx.x, warp = tid >> 5;
-  // shared layout: B hi | B lo | sptr | V | acc | long-piece partials | tile table | carry
+  // shared layout: B hi | B lo | U = (A hi | A lo) or V | sptr | acc | long-piece partials | tiles | carry
   uint32_t* sBhi = reinterpret_cast<uint32_t*>(smem_raw);
   uint32_t* sBlo = reinterpret_cast<uint32_t*>(smem_raw + tp.btile);
-  const TaskSmem<T> ts = carve_task_smem<T>(smem_raw, 2 * tp.btile, TASK, L, KMAX, P, NT);
+  unsigned char* U = smem_raw + 2 * tp.btile;
+  uint32_t* sAhi = reinterpret_cast<uint32_t*>(U);
+  uint32_t* sAlo = reinterpret_cast<uint32_t*>(U + tp.atile);
+  const TaskSmem<T> ts =
+      carve_task_smem<T>(smem_raw, 2 * tp.btile + tp.ubytes, TASK, L, KMAX, P, NT, reinterpret_cast<T*>(U));
 
   // B tiles from the permuted core gp[((o_full * Jf + cf) * JN + j]: element (n, k) with
-  // n = o * CS + j, k = s0 * jf8 + cf (s0 = 0 when na = 1), o_full = o (na = 1) or s0 + JA1 o
+  // n = o * JN + j, k = s0 * jf8 + cf (s0 = 0 when na = 1), o_full = o (na = 1) or s0 + JA1 o
   for (int e = tid; e < tp.Np * tp.Kp; e += blockDim.x) {
     const int n = e / tp.Kp, k = e - n * tp.Kp;
-    const int o = n / CS, j = n - o * CS;
+    const int o = n / JN, j = n - o * JN;
     const int s0 = NA == 2 ? k / tp.jf8 : 0, cf = NA == 2 ? k - s0 * tp.jf8 : k;
     float v = 0.f;
     if (j < r.Jn && cf < r.Jf && o < tp.O && s0 < tp.JA1) {
@@ -396,12 +414,15 @@ __global__ void __launch_bounds__(128, 2) sweep_task_tc_kernel(DevModel<float> M
     }
     uint32_t hi, lo;
     tc::split_tf32(v, hi, lo);
-    const uint32_t w = tc::kmajor_offset(n, k, tp.Kp) >> 2;
-    sBhi[w] = hi;
-    sBlo[w] = lo;
+    const uint32_t wi = tc::kmajor_offset(n, k, tp.Kp) >> 2;
+    sBhi[wi] = hi;
+    sBlo[wi] = lo;
   }
   for (int t = tid; t < NT; t += blockDim.x) sweep_tile(t, JN, r.Jn, MODE, ts.sCab[t], ts.sOut[t]);
-  if (tid == 0) tc::mbar_init(&mma_bar, 1);
+  if (tid == 0) {
+    tc::mbar_init(&mma_bar, 1);
+    wait_failed = 0;
+  }
   if (warp == 0) tc::tmem_alloc(&tmem_slot, (uint32_t)tp.ncols);
   tc::fence_async_smem();
   tc::fence_before_sync();
@@ -409,17 +430,17 @@ __global__ void __launch_bounds__(128, 2) sweep_task_tc_kernel(DevModel<float> M
   tc::fence_after_sync();
   const uint32_t tbase = tmem_slot;
   const uint32_t lane = (uint32_t)(32 * (warp & 3)) << 16;
-  const uint32_t colA = 0, colAlo = (uint32_t)tp.Kp, colD = 2u * (uint32_t)tp.Kp;
+  const uint32_t colAlo = (uint32_t)tp.Kp, colD = (uint32_t)tp.colD;
   const uint32_t idesc = tc::idesc_tf32(128, tp.Np);
   const uint32_t sbo = (uint32_t)tp.Kp * 32u;
   const uint32_t bhi_addr = tc::smem_u32(sBhi), blo_addr = tc::smem_u32(sBlo);
+  const uint32_t ahi_addr = tc::smem_u32(sAhi), alo_addr = tc::smem_u32(sAlo);
   uint32_t phase = 0;
-  bool failed = false;
 
   const int R = *csr.nnzrows;
   const int64_t nnz = csr.nnz;
   const int64_t tb = blockIdx.x * a.tpc, te = min(tb + a.tpc, a.ntasks);
-  for (int64_t task = tb; task < te && !failed; ++task) {
+  for (int64_t task = tb; task < te; ++task) {
     const int64_t t0 = task * TASK, t1 = min(t0 + (int64_t)TASK, nnz);
     const int cnt = (int)(t1 - t0);
     int64_t k0;
@@ -454,20 +475,24 @@ __global__ void __launch_bounds__(128, 2) sweep_task_tc_kernel(DevModel<float> M
       else xv[e] = valid ? static_cast<const T*>(a.resid_coo)[csr.perm[p]] : 0.f;
     }
 
+    float d[E][JN];
 #pragma unroll
     for (int g = 0; g < E; ++g) {
-      // A operand of this lane: hi at columns [0, Kp), lo at [Kp, 2 Kp)
+      // A operand of this group's entry tid: hi and lo, in shared memory (na = 1, the row is
+      // the entry, 16-byte pieces of four k) or in this lane's tensor-memory row (na = 2)
       if constexpr (NA == 1) {
 #pragma unroll
-        for (int c = 0; c < 16; c += 8) {
+        for (int c = 0; c < 16; c += 4) {
           if (c < tp.Kp) {
-            uint32_t h[8], l[8];
+            uint32_t h[4], l[4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) tc::split_tf32(a0[g][c + i], h[i], l[i]);
-            tc::st8(tbase + lane + colA + c, h);
-            tc::st8(tbase + lane + colAlo + c, l);
+            for (int i = 0; i < 4; ++i) tc::split_tf32(a0[g][c + i], h[i], l[i]);
+            const uint32_t wi = tc::kmajor_offset(tid, c, tp.Kp) >> 2;
+            *reinterpret_cast<uint4*>(sAhi + wi) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(sAlo + wi) = make_uint4(l[0], l[1], l[2], l[3]);
           }
         }
+        tc::fence_async_smem();
       } else {
 #pragma unroll
         for (int s0 = 0; s0 < 16; ++s0) {
@@ -480,14 +505,14 @@ __global__ void __launch_bounds__(128, 2) sweep_task_tc_kernel(DevModel<float> M
 #pragma unroll
                 for (int i = 0; i < 8; ++i) tc::split_tf32(a0[g][c + i] * w0, h[i], l[i]);
                 const uint32_t col = (uint32_t)(s0 * tp.jf8 + c);
-                tc::st8(tbase + lane + colA + col, h);
+                tc::st8(tbase + lane + col, h);
                 tc::st8(tbase + lane + colAlo + col, l);
               }
             }
           }
         }
+        tc::wait_st();
       }
-      tc::wait_st();
       tc::fence_before_sync();
       __syncthreads();
       if (tid == 0) {
@@ -495,52 +520,52 @@ __global__ void __launch_bounds__(128, 2) sweep_task_tc_kernel(DevModel<float> M
         for (int ks = 0; ks < tp.Kp / 8; ++ks) {
           const uint64_t bh = tc::smem_desc(bhi_addr + (uint32_t)ks * 256u, 128u, sbo);
           const uint64_t bl = tc::smem_desc(blo_addr + (uint32_t)ks * 256u, 128u, sbo);
-          tc::mma_tf32_ts(tbase + colD, tbase + colA + ks * 8, bh, idesc, ks > 0 ? 1u : 0u);
-          tc::mma_tf32_ts(tbase + colD, tbase + colA + ks * 8, bl, idesc, 1u);
-          tc::mma_tf32_ts(tbase + colD, tbase + colAlo + ks * 8, bh, idesc, 1u);
+          if constexpr (NA == 1) {
+            const uint64_t ah = tc::smem_desc(ahi_addr + (uint32_t)ks * 256u, 128u, sbo);
+            const uint64_t al = tc::smem_desc(alo_addr + (uint32_t)ks * 256u, 128u, sbo);
+            tc::mma_tf32_ss(tbase + colD, ah, bh, idesc, ks > 0 ? 1u : 0u);
+            tc::mma_tf32_ss(tbase + colD, ah, bl, idesc, 1u);
+            tc::mma_tf32_ss(tbase + colD, al, bh, idesc, 1u);
+          } else {
+            tc::mma_tf32_ts(tbase + colD, tbase + ks * 8, bh, idesc, ks > 0 ? 1u : 0u);
+            tc::mma_tf32_ts(tbase + colD, tbase + ks * 8, bl, idesc, 1u);
+            tc::mma_tf32_ts(tbase + colD, tbase + colAlo + ks * 8, bh, idesc, 1u);
+          }
         }
         tc::mma_commit(&mma_bar);
       }
       __syncwarp();
       const bool done = tc::mbar_wait_bounded(&mma_bar, phase, kTcWaitPolls);
-      if (__syncthreads_or(!done)) {
-        failed = true;
-        break;
-      }
       phase ^= 1u;
+      if (__any_sync(0xffffffffu, !done) && (tid & 31) == 0) wait_failed = 1;  // checked after the task's V barrier
       tc::fence_after_sync();
-      // stage 2: delta(j) = sum_o w(o) T[(o, j)]
-      float d[JN];
+      // stage 2: delta(j) = sum_o w(o) T[o * JN + j]
 #pragma unroll
-      for (int j = 0; j < JN; ++j) d[j] = 0.f;
+      for (int j = 0; j < JN; ++j) d[g][j] = 0.f;
+      contract_rest<JN>(tbase + lane + colD, tp.Np, tp.O, wr[g], d[g]);
+      tc::fence_before_sync();  // this group's accumulator reads before the next group's MMAs
+    }
+    // every MMA of the task has completed (each thread waited): V may take over the A region
 #pragma unroll
-      for (int o = 0; o < 16; ++o) {
-        if (o < tp.O) {
-          float v[CS];
-          tmem_load_cols<CS>(tbase + lane + colD + (uint32_t)(o * CS), v);
-#pragma unroll
-          for (int j = 0; j < JN; ++j) d[j] = fmaf(wr[g][o], v[j], d[j]);
-        }
-      }
+    for (int g = 0; g < E; ++g) {
       const int q = tid + g * 128;
       if (q < cnt) {
         T* dst = ts.sV + q * L;
 #pragma unroll
-        for (int j = 0; j < JN; ++j) dst[j] = d[j];
+        for (int j = 0; j < JN; ++j) dst[j] = d[g][j];
         dst[JN] = xv[g];
         dst[JN + 1] = T(0);
       }
-      tc::fence_before_sync();  // this group's TMEM reads before the next group's MMAs
     }
-    if (failed) break;
     __syncthreads();
+    if (wait_failed) break;  // uniform: read after the barrier
     task_row_sums<T, MODE>(a, JN, task, tb, te, t0, t1, nrows, k0, ts.sptr, NT, ts.sCab, ts.sOut, ts.sV, ts.sAcc,
                            ts.sPart, &pscr, cin, cout);
   }
-  if (failed) {
-    // the MMAs may still be in flight: give them another bounded wait before TMEM is freed
+  if (wait_failed) {
+    // the MMAs may still be in flight: give them another bounded wait before tensor memory is freed
     if (tid == 0) atomicOr(&g_sweep_status, 1u);
-    tc::mbar_wait_bounded(&mma_bar, phase, kTcWaitPolls);
+    tc::mbar_wait_bounded(&mma_bar, phase ^ 1u, kTcWaitPolls);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -635,12 +660,12 @@ static int pieces_per_round(int P) {
 }
 
 template <typename T>
-static size_t task_smem(int task, int kmax, int JN, int P, int mode, size_t core_bytes) {
+static size_t task_smem(int task, int kmax, int JN, int P, int mode, size_t core_bytes, bool own_v = true) {
   const int NT = sweep_tiles(JN, mode);
   size_t off = (core_bytes + 15) & ~(size_t)15;
   off += (size_t)(task + 2) * 8;
   off = (off + 15) & ~(size_t)15;
-  off += (size_t)task * (JN + 2) * sizeof(T);
+  if (own_v) off += (size_t)task * (JN + 2) * sizeof(T);
   off = (off + 15) & ~(size_t)15;
   off += (size_t)kmax * P * sizeof(T);
   off += (size_t)long_chunks(task) * NT * 4 * sizeof(T);
@@ -721,7 +746,6 @@ static bool tensor_cores_enabled() {
 
 static bool tc_plan(const ModeRoles& r, int order, int JN, TcPlan* out) {
   if (!tensor_cores_enabled()) return false;
-  const int CS = JN <= 8 ? 8 : (JN <= 16 ? 16 : 32);
   int best = 1 << 30;
   bool found = false;
   for (int na = 1; na <= 2; ++na) {
@@ -739,11 +763,16 @@ static bool tc_plan(const ModeRoles& r, int order, int JN, TcPlan* out) {
     p.Kp = p.jf8 * ja1;
     p.O = jr;
     p.has_rest = nrest;
-    p.Np = (jr * CS + 15) / 16 * 16;
-    if (2 * p.Kp + p.Np > 256) continue;
+    p.Np = (jr * JN + 15) / 16 * 16;
+    if (p.Np > kTcMaxChunks * 16) continue;
+    p.colD = na == 1 ? 0 : 2 * p.Kp;
+    if (p.colD + p.Np > 256) continue;
     p.ncols = 32;
-    while (p.ncols < 2 * p.Kp + p.Np) p.ncols *= 2;
+    while (p.ncols < p.colD + p.Np) p.ncols *= 2;
+    p.per_sm = 512 / p.ncols;
     p.btile = (size_t)p.Np * p.Kp * 4;
+    p.atile = na == 1 ? (size_t)128 * p.Kp * 4 : 0;
+    p.ubytes = align_up(std::max(2 * p.atile, (size_t)kTask * (JN + 2) * 4), 128);
     const int cost = jr * JN + (na == 2 ? 3 : 2) * p.Kp;
     if (cost < best) {
       best = cost;
@@ -755,13 +784,13 @@ static bool tc_plan(const ModeRoles& r, int order, int JN, TcPlan* out) {
 }
 
 template <int JN, int MODE>
-static vest_status launch_tc(const DevModel<float>& M, const DevMode<float>& csr, const float* gp, const SweepArgs& a,
+static vest_status launch_tc(const DevModel<float>& M, const DevMode<float>& csr, const float* gp, SweepArgs a,
                              const TcPlan& tp, cudaStream_t s) {
-  size_t smem = task_smem<float>(a.task, a.kmax, JN, a.P, MODE, 2 * tp.btile);
+  a.kmax = std::min(a.kmax, 32);  // fewer row pieces per round: room for four CTAs per SM
+  size_t smem = task_smem<float>(a.task, a.kmax, JN, a.P, MODE, 2 * tp.btile + tp.ubytes, false);
   // no more CTAs on an SM than its 512 TMEM columns hold, so no allocation ever waits
-  const int per_sm = 512 / tp.ncols;
   const size_t sm_bytes = 228 * 1024, reserved = 1024;
-  smem = std::max(smem, sm_bytes / (per_sm + 1) - reserved + 16);
+  smem = std::max(smem, sm_bytes / (tp.per_sm + 1) - reserved + 16);
   if (smem > kSmemMax) return fail(VEST_ERR_UNSUPPORTED, "tensor-core factor sweep: shared memory exceeds 227 KB");
   auto kern = tp.na == 2 ? sweep_task_tc_kernel<JN, MODE, 2> : sweep_task_tc_kernel<JN, MODE, 1>;
   VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

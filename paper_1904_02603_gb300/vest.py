@@ -72,6 +72,7 @@ _SIGS = {
     "vest_index_destroy": (C.c_int, [_P]),
     "vest_index_mode": (C.c_int, [_P, C.c_int32, C.POINTER(vest_mode_view)]),
     "vest_scratch_bytes": (C.c_size_t, [_P, C.POINTER(vest_model)]),
+    "vest_scratch_bytes_for": (C.c_size_t, [C.POINTER(vest_tensor), C.POINTER(vest_model)]),
     "vest_sweep_factors": (C.c_int, [_P, C.POINTER(vest_model), C.c_int32, C.c_double, C.c_int32, _P,
                                      C.c_size_t, _P]),
     "vest_sweep_core": (C.c_int, [_P, C.POINTER(vest_model), C.c_int32, C.c_double, _P, C.c_size_t, _P]),
@@ -90,6 +91,7 @@ _SIGS = {
     "vest_reconstruct": (C.c_int, [C.POINTER(vest_model), _P, C.c_int64, _P, _P]),
     "vest_loss_noalloc": (C.c_int, [_P, C.POINTER(vest_model), C.c_int32, C.c_double, _P, _P, _P]),
     "vest_device_status": (C.c_int, [C.POINTER(C.c_uint32), C.c_int32]),
+    "vest_probe_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), _P, C.c_size_t, _P]),
 }
 
 _lib = None
@@ -281,6 +283,17 @@ def vest_device_status(clear: bool = True) -> int:
     return int(f.value)
 
 
+PROBE_FP32_FMA, PROBE_FP64_FMA, PROBE_TF32_MMA, PROBE_L2_GATHER = 0, 1, 2, 3
+
+
+def vest_probe_peak(kind: int, buffer: torch.Tensor | None = None, stream=None) -> float:
+    """Measured peak rate of one unit (TFLOP/s for kinds 0-2, TB/s for the L2 gather, kind 3)."""
+    r = C.c_double(0.0)
+    _call("vest_probe_peak", int(kind), C.byref(r), _dptr(buffer), buffer.numel() * buffer.element_size()
+          if buffer is not None else 0, _stream(stream))
+    return float(r.value)
+
+
 def vest_launch_count() -> int:
     return int(load().vest_launch_count())
 
@@ -300,6 +313,38 @@ def vest_build_index(t: Tensor, stream=None) -> Index:
 
 def vest_scratch_bytes(ix: Index, m: Model) -> int:
     return int(load().vest_scratch_bytes(ix.handle, C.byref(m.cstruct())))
+
+
+def vest_scratch_bytes_for(t: Tensor, m: Model) -> int:
+    """vest_scratch_bytes for the index that vest_build_index(t) would make, without building it."""
+    return int(load().vest_scratch_bytes_for(C.byref(t.cstruct()), C.byref(m.cstruct())))
+
+
+def _shape_structs(dims, ranks, nnz: int, dtype):
+    t, m = vest_tensor(), vest_model()
+    t.order = m.order = len(dims)
+    t.val_dtype = m.dtype = _dtype_code(dtype)
+    t.nnz = int(nnz)
+    for n, (d, r) in enumerate(zip(dims, ranks)):
+        t.dims[n] = m.dims[n] = int(d)
+        m.ranks[n] = int(r)
+    return t, m
+
+
+def device_bytes_for_shape(dims, ranks, nnz: int, dtype=torch.float32) -> dict:
+    """Device memory a factorisation of this shape takes, from the library's own size queries,
+    before anything is allocated: the tensor (indices and values), the index workspace, the
+    scratch and the model (factors, core and their masks), in bytes."""
+    t, m = _shape_structs(dims, ranks, nnz, dtype)
+    es = torch.empty(0, dtype=dtype).element_size()
+    G = 1
+    for r in ranks:
+        G *= int(r)
+    model = sum(int(d) * int(r) * (es + 1) for d, r in zip(dims, ranks)) + G * (es + 1)
+    return {"tensor": int(nnz) * (4 * len(dims) + es),
+            "index": int(load().vest_index_workspace_bytes(C.byref(t))),
+            "scratch": int(load().vest_scratch_bytes_for(C.byref(t), C.byref(m))),
+            "model": model}
 
 
 def vest_autosearch_scratch_bytes(ix: Index, m: Model) -> int:

@@ -51,3 +51,27 @@ def test_served_results_equal_alone_results():
             np.testing.assert_array_equal(r.result, ref)
     st = S.latency_stats(reqs)
     assert st["requests"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0
+
+
+def test_budget_holds_and_evicts_resident_models():
+    """A budget that holds one job and a few models: the server never admits past it, evicts the
+    least recently used models no waiting request needs, and every answered request still equals
+    its alone result."""
+    specs = _specs()
+    reqs = S.make_trace(specs, rate=400.0, duration=0.08, seed=7)
+    server = S.Server(specs, slots=4, sweeps=3)
+    job_max = max(j for j, _ in server.sizes)
+    model_min = min(m for _, m in server.sizes)
+    query_max = max(16 * r.q_idx.size for r in reqs if r.kind == "query")
+    server.budget_bytes = job_max + query_max + 2 * model_min
+    server.serve(reqs)
+    torch.cuda.synchronize()
+    assert server.max_used_bytes <= server.budget_bytes
+    assert server.evicted, "the small budget should force evictions"
+    for r in reqs:
+        if r.kind == "query" and not r.evicted:
+            mdl, _ = _alone(specs[reqs[r.target].spec], 3)
+            ref = V.vest_reconstruct(mdl, torch.from_numpy(r.q_idx).cuda()).cpu().numpy()
+            np.testing.assert_array_equal(r.result, ref)
+        if r.kind == "query" and r.evicted:
+            assert r.result is None and r.target in server.evicted

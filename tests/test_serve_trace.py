@@ -39,3 +39,21 @@ def test_latency_stats():
     st = S.latency_stats(reqs)
     assert st["requests"] == 2 and st["jobs"] == 1 and st["queries"] == 1
     assert abs(st["p50_ms"] - 625.0) < 1e-9 and st["span_s"] == 1.0 and st["jobs_per_s"] == 1.0
+
+
+def test_budget_counts_resident_models_and_evicts_least_recently_used_unpinned():
+    b = S.Budget(100)
+    b.reserve(30)
+    assert b.fits(70) and not b.fits(71)
+    b.release(30)
+    for rid, nb in ((1, 20), (2, 20), (3, 20)):
+        b.add_resident(rid, nb)
+    assert b.used == 60
+    b.touch(1)  # order of use now 2, 3, 1
+    assert b.make_room(30, pinned=set()) == []  # 60 + 30 fits
+    assert b.make_room(50, pinned={2}) == [3]  # 2 is pinned: 3 goes, then 40 + 50 fits
+    assert list(b.resident) == [2, 1] and b.used == 40
+    b.reserve(50)
+    assert b.make_room(30, pinned={1, 2}) == [] and not b.fits(30)  # nothing may go
+    b.release(50)
+    assert b.used == 40
