@@ -5,7 +5,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 
 #include "delta.cuh"
 
@@ -39,6 +42,30 @@ int num_sms() {
   if (cudaGetDevice(&dev) != cudaSuccess) return 148;
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 148;
   return n;
+}
+
+vest_status max_dynamic_smem(const void* kern, size_t* out) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> cache;
+  int dev = 0;
+  VEST_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find({dev, kern});
+    if (it != cache.end()) {
+      *out = it->second;
+      return VEST_OK;
+    }
+  }
+  int optin = 0;
+  VEST_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa{};
+  VEST_CUDA(cudaFuncGetAttributes(&fa, kern));
+  const size_t cap = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  std::lock_guard<std::mutex> lock(mu);
+  cache[{dev, kern}] = cap;
+  *out = cap;
+  return VEST_OK;
 }
 
 static size_t dtype_size(int dt) { return dt == VEST_F64 ? 8 : 4; }

@@ -1006,7 +1006,7 @@ static vest_status launch_gram(const DevModel<T>& M, const DevMode<T>& csr, cons
                                cudaStream_t s) {
   const size_t smem = smem_gram<T>(ga.mq, SGB);
   auto kern = core_gram_pass_kernel<T, SGB>;
-  VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VEST_TRY(allow_smem(kern, smem));
   kern<<<grid, 256, smem, s>>>(M, csr, ga);
   VEST_LAUNCH("core_gram_pass_kernel");
   return VEST_OK;
@@ -1037,7 +1037,7 @@ template <typename T, int J0B>
 static vest_status launch_stats(const DevModel<T>& M, const DevMode<T>& csr, const T* r, const T* A0c,
                                 const StatsArgs& a, bool diag, int grid, int nwarps, size_t smem, cudaStream_t s) {
   auto kern = diag ? core_stats_kernel<T, J0B, true> : core_stats_kernel<T, J0B, false>;
-  VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VEST_TRY(allow_smem(kern, smem));
   kern<<<grid, 32 * nwarps, smem, s>>>(M, csr, r, A0c, a);
   VEST_LAUNCH("core_stats_kernel");
   return VEST_OK;
@@ -1165,7 +1165,7 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
                                                                          num_sms() * 8)),
                          256, 0, s>>>(M, csr.nzrow, csr.nnzrows, c.J0, A0c);
     VEST_LAUNCH("core_a0c_kernel");
-    VEST_CUDA(cudaFuncSetAttribute(core_g_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    VEST_TRY(allow_smem(core_g_pass_kernel<T>, gsm));
   }
   int64_t iblk = 0;
   for (int64_t sfx = 0; sfx < c.S; ++sfx) {
@@ -1189,7 +1189,7 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
       }
       const size_t ssm = (size_t)(blk.b * (blk.b + 1) / 2) * 8;
       auto sk = core_solve_kernel<T>;
-      VEST_CUDA(cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+      VEST_TRY(allow_smem(sk, ssm));
       sk<<<1, 256, ssm, s>>>(M, blk, c.J0, c.J1, reg, lambda, bf.gram + iblk * c.nmmax, gvec, dbuf[iblk & 1]);
       VEST_LAUNCH("core_solve_kernel");
       a.prev = blk;

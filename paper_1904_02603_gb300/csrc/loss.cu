@@ -159,7 +159,7 @@ template <typename T, int JN, int JF, int NSLOW, int E>
 static vest_status launch_loss(const DevModel<T>& M, const DevMode<T>& csr, const T* gp, const LossArgs& a,
                                size_t smem, int grid, T* r0, T* rc, cudaStream_t s) {
   auto kern = loss_kernel<T, JN, JF, NSLOW, E>;
-  VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VEST_TRY(allow_smem(kern, smem));
   kern<<<grid, kLossTask / E, smem, s>>>(M, csr, gp, a, r0, rc);
   VEST_LAUNCH("loss_kernel");
   return VEST_OK;

@@ -134,7 +134,7 @@ extern "C" vest_status vest_probe_peak(int32_t kind, double* rate, void* buffer,
     } else if (kind == 2) {
       const int count = 8192, blocks = sms;
       const int pad = 120 * 1024;  // more than half of an SM's shared memory: one CTA per SM
-      VEST_CUDA(cudaFuncSetAttribute(mma_tf32_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pad));
+      VEST_TRY(allow_smem(mma_tf32_probe_kernel, pad));
       mma_tf32_probe_kernel<<<blocks, 128, pad, s>>>(count, status);
       VEST_LAUNCH("mma_tf32_probe_kernel");
       work = 2.0 * 128 * 256 * 8 * (double)count * blocks;  // flops

@@ -205,43 +205,37 @@ __device__ __forceinline__ void task_row_sums(const SweepArgs& a, int JN, int64_
     // phase 2: per-row sums over the task's pieces r0 .. r0 + nr - 1
     piece_sums<T, MODE == kModeResp>(sptr + r0, nr, t0, t1, NT, P, sCab, sOut, sV, L, JN, sAcc, sPart, pscr);
     // phase 3: store the sums of rows that end here; carry a row that continues into
-    // the block's next task; spill rows cut by the edges of the block's task range
-    for (int kr = threadIdx.x; kr < nr; kr += blockDim.x) {
+    // the block's next task; spill rows cut by the edges of the block's task range.  One
+    // thread per (row, output): the P outputs of a row are independent, so a row carried
+    // across tasks costs one Kahan step per thread, not P in a row on one thread.
+    for (int idx = threadIdx.x; idx < nr * P; idx += blockDim.x) {
+      const int kr = idx / P, i = idx - kr * P;
       const int k = r0 + kr;
       const int64_t rs = sptr[k], re = sptr[k + 1];
-      const T* piece = sAcc + kr * P;
+      const T pv = sAcc[kr * P + i];
       const bool carried_in = (k == 0) && rs < t0 && task > tb;  // earlier pieces are in cin
       const bool continues = re > t1;
       const bool started_here = rs >= rt0;
       if (!continues && !carried_in && rs >= t0) {
-        T* dst = a.rowbuf_t<T>() + (size_t)(k0 + k) * P;
-        for (int i = 0; i < P; ++i) dst[i] = piece[i];
+        a.rowbuf_t<T>()[(size_t)(k0 + k) * P + i] = pv;
       } else {
         // running sums of a row cut by task edges: (sum, compensation) in T
         T* as = continues ? cout : cin;
-        T* ac = as + P;
-        for (int i = 0; i < P; ++i) {
-          T sum = carried_in ? cin[i] : T(0), cmp = carried_in ? cin[P + i] : T(0);
-          const T y = piece[i] - cmp;
-          const T t = sum + y;
-          ac[i] = (t - sum) - y;
-          as[i] = t;
-        }
+        const T sum = carried_in ? cin[i] : T(0), cmp = carried_in ? cin[P + i] : T(0);
+        const T y = pv - cmp;
+        const T t = sum + y;
+        const T c = (t - sum) - y;
+        as[P + i] = c;
+        as[i] = t;
         if (!continues) {
-          if (started_here) {
-            T* dst = a.rowbuf_t<T>() + (size_t)(k0 + k) * P;
-            for (int i = 0; i < P; ++i) dst[i] = as[i] - ac[i];
-          } else {  // the row entered the block's range from an earlier block: incoming partial
-            double* sp = a.spill + ((size_t)blockIdx.x * 2 + 0) * P;
-            for (int i = 0; i < P; ++i) sp[i] = (double)as[i] - (double)ac[i];
-          }
+          if (started_here) a.rowbuf_t<T>()[(size_t)(k0 + k) * P + i] = t - c;
+          else a.spill[((size_t)blockIdx.x * 2 + 0) * P + i] = (double)t - (double)c;  // incoming partial
         } else if (task + 1 == te) {  // leaves the block's range
-          double* sp = a.spill + ((size_t)blockIdx.x * 2 + (started_here ? 1 : 0)) * P;
-          for (int i = 0; i < P; ++i) sp[i] = (double)as[i] - (double)ac[i];
-          a.spanning[blockIdx.x] = started_here ? (int32_t)(k0 + k) : -1;
+          a.spill[((size_t)blockIdx.x * 2 + (started_here ? 1 : 0)) * P + i] = (double)t - (double)c;
         }
       }
-      if (k == nrows - 1 && task + 1 == te && !(continues && started_here)) a.spanning[blockIdx.x] = -1;
+      if (i == 0 && k == nrows - 1 && task + 1 == te)
+        a.spanning[blockIdx.x] = (continues && started_here) ? (int32_t)(k0 + k) : -1;
     }
     __syncthreads();
   }
@@ -440,21 +434,19 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
   const int R = *csr.nnzrows;
   const int64_t nnz = csr.nnz;
   const int64_t tb = blockIdx.x * a.tpc, te = min(tb + a.tpc, a.ntasks);
-  for (int64_t task = tb; task < te; ++task) {
-    const int64_t t0 = task * TASK, t1 = min(t0 + (int64_t)TASK, nnz);
-    const int cnt = (int)(t1 - t0);
-    int64_t k0;
-    const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, ts.sptr, &k0);
-    T* cin = ts.sCarry + (task & 1) * 2 * P;
-    T* cout = ts.sCarry + ((task + 1) & 1) * 2 * P;
 
-    // gathers for both entries of the thread: rows of the A modes, the remaining mode's row, X (or r)
-    float a0[E][16], a1[E][NA == 2 ? 16 : 1], wr[E][16], xv[E];
+  // gathers for both entries of the thread in task `tk`: rows of the A modes, the remaining
+  // mode's row, X (or r).  The next task's are issued before the current task's row sums, so
+  // their latency hides behind that phase.
+  float a0[E][16], a1[E][NA == 2 ? 16 : 1], wr[E][16], xv[E];
+  auto gather = [&](int64_t tk) {
+    const int64_t g0 = tk * TASK;
+    const int gcnt = (int)(min(g0 + (int64_t)TASK, nnz) - g0);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int q = tid + e * 128;
-      const bool valid = q < cnt;
-      const int64_t p = t0 + (valid ? q : 0);
+      const bool valid = q < gcnt;
+      const int64_t p = g0 + (valid ? q : 0);
       const float* ra0 = M.A[r.f] + (int64_t)csr.oidx[p] * r.Jf;
 #pragma unroll
       for (int i = 0; i < 16; ++i) a0[e][i] = (valid && i < r.Jf) ? __ldg(ra0 + i) : 0.f;
@@ -474,6 +466,16 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
       if constexpr (MODE == kModeUpdate) xv[e] = valid ? csr.val[p] : 0.f;
       else xv[e] = valid ? static_cast<const T*>(a.resid_coo)[csr.perm[p]] : 0.f;
     }
+  };
+  if (tb < te) gather(tb);
+
+  for (int64_t task = tb; task < te; ++task) {
+    const int64_t t0 = task * TASK, t1 = min(t0 + (int64_t)TASK, nnz);
+    const int cnt = (int)(t1 - t0);
+    int64_t k0;
+    const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, ts.sptr, &k0);
+    T* cin = ts.sCarry + (task & 1) * 2 * P;
+    T* cout = ts.sCarry + ((task + 1) & 1) * 2 * P;
 
     float d[E][JN];
 #pragma unroll
@@ -557,6 +559,7 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
         dst[JN + 1] = T(0);
       }
     }
+    if (task + 1 < te) gather(task + 1);
     __syncthreads();
     if (wait_failed) break;  // uniform: read after the barrier
     task_row_sums<T, MODE>(a, JN, task, tb, te, t0, t1, nrows, k0, ts.sptr, NT, ts.sCab, ts.sOut, ts.sV, ts.sAcc,
@@ -693,7 +696,7 @@ template <typename T, int JN, int JF, int NSLOW, int MODE, int E>
 static vest_status launch_task(const DevModel<T>& M, const DevMode<T>& csr, const T* gp, const SweepArgs& a,
                                size_t smem, cudaStream_t s) {
   auto kern = sweep_task_kernel<T, JN, JF, NSLOW, MODE, E>;
-  VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VEST_TRY(allow_smem(kern, smem));
   kern<<<(unsigned)ceil_div(a.ntasks, a.tpc), a.task / E, smem, s>>>(M, csr, gp, a);
   VEST_LAUNCH("sweep_task_kernel");
   return VEST_OK;
@@ -793,7 +796,7 @@ static vest_status launch_tc(const DevModel<float>& M, const DevMode<float>& csr
   smem = std::max(smem, sm_bytes / (tp.per_sm + 1) - reserved + 16);
   if (smem > kSmemMax) return fail(VEST_ERR_UNSUPPORTED, "tensor-core factor sweep: shared memory exceeds 227 KB");
   auto kern = tp.na == 2 ? sweep_task_tc_kernel<JN, MODE, 2> : sweep_task_tc_kernel<JN, MODE, 1>;
-  VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VEST_TRY(allow_smem(kern, smem));
   kern<<<(unsigned)ceil_div(a.ntasks, a.tpc), 128, smem, s>>>(M, csr, gp, a, tp);
   VEST_LAUNCH("sweep_task_tc_kernel");
   return VEST_OK;
@@ -865,7 +868,7 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
   }
   const size_t fsmem = (size_t)std::max(1, 256 / a.P) * a.P * 8 + 8 * a.P;
   auto fk = sweep_fixup_kernel<T, MODE>;
-  VEST_CUDA(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+  VEST_TRY(allow_smem(fk, fsmem));
   const int64_t fgrid = std::min<int64_t>(nblocks, (int64_t)num_sms() * 8);
   fk<<<(unsigned)fgrid, 256, fsmem, s>>>(M, csr, a, (int)nblocks);
   VEST_LAUNCH("sweep_fixup_kernel");

@@ -152,6 +152,23 @@ inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 int num_sms();
 
+// Largest dynamic shared memory `kern` may take: the device's opt-in maximum per CTA (227 KB
+// on sm_103) less the kernel's static shared memory; looked up once per kernel and device.
+vest_status max_dynamic_smem(const void* kern, size_t* out);
+
+// Lets `kern` launch with dynamic shared memory up to that maximum; `need` is what the coming
+// launch asks for (checked against it).  The attribute is set to the one fixed maximum, never
+// to `need`: host threads that launch the same kernel with different sizes at the same time
+// then cannot narrow the bound under each other's launches.
+template <typename K>
+inline vest_status allow_smem(K kern, size_t need) {
+  size_t cap = 0;
+  VEST_TRY(max_dynamic_smem(reinterpret_cast<const void*>(kern), &cap));
+  if (need > cap) return fail(VEST_ERR_UNSUPPORTED, "a kernel needs more shared memory than a CTA may have");
+  VEST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+  return VEST_OK;
+}
+
 // Argument checks shared by every entry point that takes an index and a model:
 // order, dtype, ranks, dims, pointers and the size limits of the library.
 vest_status check_pair(const vest_index* ix, const vest_model* m);
