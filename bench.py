@@ -424,7 +424,19 @@ def main_batch(args):
     time.sleep(0.5)
     batched_ms = timed(run.replay, steps)
     launches = per_replay * steps
+    # the autotuned batched form: per shape class, the faster kernel for Eq. 11 from trial sweeps
+    tuned = B.prepare(specs)
+    t_tune = time.perf_counter()
+    table = B.autotune(tuned)
+    tune_s = time.perf_counter() - t_tune
+    captured1 = V.vest_launch_count()
+    run_t = B.BatchedRun(tuned, BATCH_SWEEPS, n_streams=args.streams)
+    launches = (V.vest_launch_count() - captured1) * steps  # the timed (autotuned) replays
+    for _ in range(warm):
+        run_t.replay()
+    tuned_ms = timed(run_t.replay, steps)
     clk = clocks.stop()
+    choices = [v["path"] for v in table.values()]
     # e2e: host inputs of one job copied in, indexed, swept and its loss read back, job by job
     # (the serving path a caller without resident data takes)
     idx_h = [torch.from_numpy(t.idx).pin_memory() for t, _, _, _ in specs[:32]]
@@ -444,17 +456,24 @@ def main_batch(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t_e
     line = {
-        "metric": "jobs/s (batched factorisations, 10 sweeps each)", "value": len(ws) / (batched_ms / 1e3),
-        "unit": "jobs/s", "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": batched_ms,
+        "metric": "jobs/s (batched factorisations, 10 sweeps each)", "value": len(ws) / (tuned_ms / 1e3),
+        "unit": "jobs/s", "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": tuned_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": BATCH, "jobs": len(ws), "sweeps": BATCH_SWEEPS, "entries": entries,
-                   "streams": args.streams, "form": "one CUDA graph per job, replayed round-robin over streams",
+                   "streams": args.streams,
+                   "form": "one CUDA graph per job, replayed round-robin over streams; the kernel for Eq. 11 "
+                           "chosen per shape class by the autotuner (batch.autotune)",
                    "l2": "the batch's CSR arrays and factors (several GB) exceed the 129 MB L2",
                    "input_generation_s": gen_s},
         "plain": {"value": len(ws) / (plain_ms / 1e3), "unit": "jobs/s", "ms_per_step": plain_ms,
                   "form": "one job after another on one stream, each call launched as it goes"},
-        "speedup_vs_plain": plain_ms / batched_ms,
-        "entry_mode_updates_per_s": sum(w.nnz * len(w.dims) for w in ws) * BATCH_SWEEPS / (batched_ms / 1e3),
+        "untuned": {"value": len(ws) / (batched_ms / 1e3), "unit": "jobs/s", "ms_per_step": batched_ms,
+                    "form": "the same graphs with the library's default kernel choice (tensor cores wherever they "
+                            "apply)"},
+        "autotune": {"classes": len(table), "tensor_core_classes": sum(1 for c in choices if c == V.DELTA_AUTO),
+                     "fma_classes": sum(1 for c in choices if c == V.DELTA_FMA), "seconds": tune_s},
+        "speedup_vs_plain": plain_ms / tuned_ms,
+        "entry_mode_updates_per_s": sum(w.nnz * len(w.dims) for w in ws) * BATCH_SWEEPS / (tuned_ms / 1e3),
         "e2e": {"value": 32 / e2e_s, "unit": "jobs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "includes": "32 jobs one by one: H2D of idx+val, index build, 10 sweeps, D2H of the loss"},
         "clocks": clk,

@@ -200,6 +200,19 @@ size_t vest_scratch_bytes_for(const vest_tensor* t, const vest_model* m);
 vest_status vest_sweep_factors(const vest_index* ix, vest_model* m, int32_t reg, double lambda,
                                int32_t mode, void* scratch, size_t scratch_bytes, void* stream);
 
+/* The factor sweep with the kernel for Eq. 11 chosen by the caller (an autotuner, for one):
+ *   VEST_DELTA_AUTO    the tensor cores (split-TF32 tcgen05 MMA, FP32 models) where they
+ *                      apply, the FMA kernels elsewhere; what vest_sweep_factors does
+ *   VEST_DELTA_FMA     the FMA kernels everywhere
+ *   VEST_DELTA_TENSOR  the tensor cores, or VEST_ERR_UNSUPPORTED (before anything is
+ *                      enqueued) where they do not apply: FP64 models, a rank above 16, or
+ *                      more than one other mode left after the one or two "A" modes
+ * All paths compute the same update to within FP32 rounding (FP64 models: bit-identical,
+ * the FMA kernels).  The environment variable VEST_TENSOR_CORES=0 turns AUTO into FMA. */
+typedef enum { VEST_DELTA_AUTO = 0, VEST_DELTA_FMA = 1, VEST_DELTA_TENSOR = 2 } vest_delta_path;
+vest_status vest_sweep_factors_ex(const vest_index* ix, vest_model* m, int32_t reg, double lambda, int32_t mode,
+                                  int32_t path, void* scratch, size_t scratch_bytes, void* stream);
+
 /* ---- a5: core sweep (Lemma 2, Eq. 12 for L_F; Lemma 4, Eq. 14 for L_1).
  * Sequential CD over the unpruned core elements in linear order; results
  * equal, in exact arithmetic, one element at a time (Section 3.5). */

@@ -271,6 +271,12 @@ size_t vest_scratch_bytes_for(const vest_tensor* t, const vest_model* m) {
 
 vest_status vest_sweep_factors(const vest_index* ix, vest_model* m, int32_t reg, double lambda, int32_t mode,
                                void* scratch, size_t scratch_bytes, void* stream) {
+  return vest_sweep_factors_ex(ix, m, reg, lambda, mode, VEST_DELTA_AUTO, scratch, scratch_bytes, stream);
+}
+
+vest_status vest_sweep_factors_ex(const vest_index* ix, vest_model* m, int32_t reg, double lambda, int32_t mode,
+                                  int32_t path, void* scratch, size_t scratch_bytes, void* stream) {
+  if (path < VEST_DELTA_AUTO || path > VEST_DELTA_TENSOR) return fail(VEST_ERR_INVALID, "unknown delta path");
   VEST_TRY(check_pair(ix, m));
   VEST_TRY(check_lambda(lambda));
   if (reg != VEST_REG_LF && reg != VEST_REG_L1) return fail(VEST_ERR_INVALID, "unknown regulariser");
@@ -280,9 +286,15 @@ vest_status vest_sweep_factors(const vest_index* ix, vest_model* m, int32_t reg,
   const cudaStream_t s = as_stream(stream);
   char* sc = static_cast<char*>(scratch);
   const int first = mode < 0 ? 0 : mode, last = mode < 0 ? m->order - 1 : mode;
+  if (path == VEST_DELTA_TENSOR)
+    for (int n = first; n <= last; ++n)
+      if (!sweep_tc_applies(m, n))
+        return fail(VEST_ERR_UNSUPPORTED, "the tensor-core delta does not apply to mode " + std::to_string(n) +
+                                              " (FP64, a rank above 16, or more than one other mode left after "
+                                              "the A modes)");
   for (int n = first; n <= last; ++n) {
-    if (m->dtype == VEST_F64) VEST_TRY(sweep_factors_mode<double>(ix, m, reg, lambda, n, sc, plan, s));
-    else VEST_TRY(sweep_factors_mode<float>(ix, m, reg, lambda, n, sc, plan, s));
+    if (m->dtype == VEST_F64) VEST_TRY(sweep_factors_mode<double>(ix, m, reg, lambda, n, sc, plan, s, path));
+    else VEST_TRY(sweep_factors_mode<float>(ix, m, reg, lambda, n, sc, plan, s, path));
   }
   return VEST_OK;
 }

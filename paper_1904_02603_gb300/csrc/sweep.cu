@@ -33,6 +33,7 @@ enum { kModeUpdate = 0, kModeResp = 1 };
 
 struct SweepArgs {
   ModeRoles r;
+  int path;  // vest_delta_path: 0 tensor cores where they apply, 1 FMA kernels, 2 tensor cores required
   int reg;
   double lambda;
   int64_t ntasks;
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
   using T = float;
   constexpr int E = 2;  // entries per thread: two groups of 128
   constexpr int L = JN + 2;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char tc_smem_raw[];
   __shared__ uint64_t mma_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int wait_failed;
@@ -387,13 +388,13 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
   const int NT = sweep_tiles(JN, MODE);
   const int tid = threadIdx.x, warp = tid >> 5;
   // shared layout: B hi | B lo | U = (A hi | A lo) or V | sptr | acc | long-piece partials | tiles | carry
-  uint32_t* sBhi = reinterpret_cast<uint32_t*>(smem_raw);
-  uint32_t* sBlo = reinterpret_cast<uint32_t*>(smem_raw + tp.btile);
-  unsigned char* U = smem_raw + 2 * tp.btile;
+  uint32_t* sBhi = reinterpret_cast<uint32_t*>(tc_smem_raw);
+  uint32_t* sBlo = reinterpret_cast<uint32_t*>(tc_smem_raw + tp.btile);
+  unsigned char* U = tc_smem_raw + 2 * tp.btile;
   uint32_t* sAhi = reinterpret_cast<uint32_t*>(U);
   uint32_t* sAlo = reinterpret_cast<uint32_t*>(U + tp.atile);
   const TaskSmem<T> ts =
-      carve_task_smem<T>(smem_raw, 2 * tp.btile + tp.ubytes, TASK, L, KMAX, P, NT, reinterpret_cast<T*>(U));
+      carve_task_smem<T>(tc_smem_raw, 2 * tp.btile + tp.ubytes, TASK, L, KMAX, P, NT, reinterpret_cast<T*>(U));
 
   // B tiles from the permuted core gp[((o_full * Jf + cf) * JN + j]: element (n, k) with
   // n = o * JN + j, k = s0 * jf8 + cf (s0 = 0 when na = 1), o_full = o (na = 1) or s0 + JA1 o
@@ -431,22 +432,35 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
   const uint32_t ahi_addr = tc::smem_u32(sAhi), alo_addr = tc::smem_u32(sAlo);
   uint32_t phase = 0;
 
-  const int R = *csr.nnzrows;
   const int64_t nnz = csr.nnz;
   const int64_t tb = blockIdx.x * a.tpc, te = min(tb + a.tpc, a.ntasks);
 
   // gathers for both entries of the thread in task `tk`: rows of the A modes, the remaining
   // mode's row, X (or r).  The next task's are issued before the current task's row sums, so
   // their latency hides behind that phase.
+  // The task's row table comes from the same prefetch: the non-empty-row number of each entry
+  // (and of the entry before each warp's first), the first and last row of the task, where the
+  // first row starts and the last one ends.
   float a0[E][16], a1[E][NA == 2 ? 16 : 1], wr[E][16], xv[E];
+  int rk[E], rkprev[E];
+  int kfirst = 0, klast = 0;
+  int64_t rs_first = 0, re_last = 0;
   auto gather = [&](int64_t tk) {
     const int64_t g0 = tk * TASK;
     const int gcnt = (int)(min(g0 + (int64_t)TASK, nnz) - g0);
+    kfirst = csr.rowk[g0];
+    klast = csr.rowk[g0 + gcnt - 1];
+    if (tid == 0) {
+      rs_first = csr.nzptr[kfirst];
+      re_last = csr.nzptr[klast + 1];
+    }
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int q = tid + e * 128;
       const bool valid = q < gcnt;
       const int64_t p = g0 + (valid ? q : 0);
+      rk[e] = csr.rowk[p];
+      rkprev[e] = (valid && q > 0 && (q & 31) == 0) ? csr.rowk[p - 1] : rk[e];
       const float* ra0 = M.A[r.f] + (int64_t)csr.oidx[p] * r.Jf;
 #pragma unroll
       for (int i = 0; i < 16; ++i) a0[e][i] = (valid && i < r.Jf) ? __ldg(ra0 + i) : 0.f;
@@ -472,8 +486,8 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
   for (int64_t task = tb; task < te; ++task) {
     const int64_t t0 = task * TASK, t1 = min(t0 + (int64_t)TASK, nnz);
     const int cnt = (int)(t1 - t0);
-    int64_t k0;
-    const int nrows = load_task_rows(csr.nzptr, csr.gran, R, t0, t1, ts.sptr, &k0);
+    const int64_t k0 = kfirst;
+    const int nrows = klast - kfirst + 1;
     T* cin = ts.sCarry + (task & 1) * 2 * P;
     T* cout = ts.sCarry + ((task + 1) & 1) * 2 * P;
 
@@ -558,6 +572,19 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
         dst[JN] = xv[g];
         dst[JN + 1] = T(0);
       }
+    }
+    // row table: sptr[k - k0] = start of every row that starts inside the task, sptr[0] and
+    // sptr[nrows] the first row's start and the last row's end (they may lie outside it)
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int q = tid + e * 128;
+      const int up = __shfl_up_sync(0xffffffffu, rk[e], 1);
+      const int before = (q & 31) == 0 ? rkprev[e] : up;
+      if (q > 0 && q < cnt && rk[e] != before) ts.sptr[rk[e] - kfirst] = t0 + q;
+    }
+    if (tid == 0) {
+      ts.sptr[0] = rs_first;
+      ts.sptr[nrows] = re_last;
     }
     if (task + 1 < te) gather(task + 1);
     __syncthreads();
@@ -748,7 +775,6 @@ static bool tensor_cores_enabled() {
 }
 
 static bool tc_plan(const ModeRoles& r, int order, int JN, TcPlan* out) {
-  if (!tensor_cores_enabled()) return false;
   int best = 1 << 30;
   bool found = false;
   for (int na = 1; na <= 2; ++na) {
@@ -857,12 +883,12 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
   }
   if (smem > kSmemMax) return fail(VEST_ERR_UNSUPPORTED, "factor sweep: shared memory of one task exceeds 227 KB");
   TcPlan tp{};
+  const bool use_tc = sizeof(T) == 4 && a.task == 256 &&
+                      (a.path == VEST_DELTA_TENSOR || (a.path == VEST_DELTA_AUTO && tensor_cores_enabled())) &&
+                      tc_plan(r, M.N, JN, &tp);
   if constexpr (sizeof(T) == 4) {
-    if (a.task == 256 && tc_plan(r, M.N, JN, &tp)) {
-      VEST_TRY(dispatch_tc<MODE>(JN, M, csr, gp, a, tp, s));
-    } else {
-      VEST_TRY(dispatch_jn<T, MODE>(JN, r.nslow, r.Jf, M, csr, gp, a, smem, s));
-    }
+    if (use_tc) VEST_TRY(dispatch_tc<MODE>(JN, M, csr, gp, a, tp, s));
+    else VEST_TRY(dispatch_jn<T, MODE>(JN, r.nslow, r.Jf, M, csr, gp, a, smem, s));
   } else {
     VEST_TRY(dispatch_jn<T, MODE>(JN, r.nslow, r.Jf, M, csr, gp, a, smem, s));
   }
@@ -880,9 +906,10 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
 
 template <typename T>
 vest_status sweep_factors_mode(const vest_index* ix, const vest_model* m, int reg, double lambda, int mode,
-                               char* scratch, const ScratchPlan& plan, cudaStream_t s) {
+                               char* scratch, const ScratchPlan& plan, cudaStream_t s, int path) {
   const DevModel<T> M = dev_model<T>(m);
   SweepArgs a{};
+  a.path = path;
   a.reg = reg;
   a.lambda = lambda;
   return run_mode<T, kModeUpdate>(ix, M, mode, a, scratch, plan, s);
@@ -904,6 +931,14 @@ vest_status responsibility_factors(const vest_index* ix, const vest_model* m, co
   return VEST_OK;
 }
 
+// Whether the tensor-core delta serves mode n of this FP32 model.
+bool sweep_tc_applies(const vest_model* m, int n) {
+  if (m->dtype != VEST_F32) return false;
+  const ModeRoles r = mode_roles(m->ranks, m->order, n);
+  TcPlan tp{};
+  return tc_plan(r, m->order, jn_bucket(r.Jn), &tp);
+}
+
 // Bits set by the factor-sweep kernels since the last clear (bit 0: a bounded wait on the
 // tensor cores gave up); synchronises the device to read them.
 vest_status sweep_device_status(uint32_t* flags, bool clear) {
@@ -919,9 +954,9 @@ vest_status sweep_device_status(uint32_t* flags, bool clear) {
 }
 
 template vest_status sweep_factors_mode<float>(const vest_index*, const vest_model*, int, double, int, char*,
-                                               const ScratchPlan&, cudaStream_t);
+                                               const ScratchPlan&, cudaStream_t, int);
 template vest_status sweep_factors_mode<double>(const vest_index*, const vest_model*, int, double, int, char*,
-                                                const ScratchPlan&, cudaStream_t);
+                                                const ScratchPlan&, cudaStream_t, int);
 template vest_status responsibility_factors<float>(const vest_index*, const vest_model*, const double*,
                                                    double* const*, double* const*, char*, const ScratchPlan&,
                                                    cudaStream_t);

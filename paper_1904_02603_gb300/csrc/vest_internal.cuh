@@ -188,10 +188,13 @@ size_t radix_hist_elems(int64_t n);
 // on the tensor cores gave up); reads them after a device synchronise, clears on request.
 vest_status sweep_device_status(uint32_t* flags, bool clear);
 
+// Whether the tensor-core delta of the FP32 factor sweep serves mode n of this model.
+bool sweep_tc_applies(const vest_model* m, int n);
+
 // Operations implemented in their own translation units.
 template <typename T>
 vest_status sweep_factors_mode(const vest_index* ix, const vest_model* m, int reg, double lambda, int mode,
-                               char* scratch, const ScratchPlan& plan, cudaStream_t s);
+                               char* scratch, const ScratchPlan& plan, cudaStream_t s, int path = VEST_DELTA_AUTO);
 template <typename T>
 vest_status responsibility_factors(const vest_index* ix, const vest_model* m, const double* stats,
                                    double* const* delta_factor, double* const* resp_factor, char* scratch,

@@ -75,6 +75,8 @@ _SIGS = {
     "vest_scratch_bytes_for": (C.c_size_t, [C.POINTER(vest_tensor), C.POINTER(vest_model)]),
     "vest_sweep_factors": (C.c_int, [_P, C.POINTER(vest_model), C.c_int32, C.c_double, C.c_int32, _P,
                                      C.c_size_t, _P]),
+    "vest_sweep_factors_ex": (C.c_int, [_P, C.POINTER(vest_model), C.c_int32, C.c_double, C.c_int32, C.c_int32, _P,
+                                        C.c_size_t, _P]),
     "vest_sweep_core": (C.c_int, [_P, C.POINTER(vest_model), C.c_int32, C.c_double, _P, C.c_size_t, _P]),
     "vest_loss": (C.c_int, [_P, C.POINTER(vest_model), C.c_int32, C.c_double, _P, _P, _P, C.c_size_t, _P]),
     "vest_responsibility": (C.c_int, [_P, C.POINTER(vest_model), _P, _P, _P, _P, _P, C.c_size_t, _P]),
@@ -358,9 +360,17 @@ def make_scratch(ix: Index, m: Model, autosearch: bool = False) -> torch.Tensor:
     return torch.empty(n, dtype=torch.uint8, device="cuda")
 
 
-def vest_sweep_factors(ix: Index, m: Model, reg: int, lam: float, mode: int, scratch: torch.Tensor, stream=None):
-    _call("vest_sweep_factors", ix.handle, C.byref(m.cstruct()), reg, lam, mode, _dptr(scratch), scratch.numel(),
-          _stream(stream))
+DELTA_AUTO, DELTA_FMA, DELTA_TENSOR = 0, 1, 2
+
+
+def vest_sweep_factors(ix: Index, m: Model, reg: int, lam: float, mode: int, scratch: torch.Tensor, stream=None,
+                       path: int = DELTA_AUTO):
+    if path == DELTA_AUTO:
+        _call("vest_sweep_factors", ix.handle, C.byref(m.cstruct()), reg, lam, mode, _dptr(scratch), scratch.numel(),
+              _stream(stream))
+    else:
+        _call("vest_sweep_factors_ex", ix.handle, C.byref(m.cstruct()), reg, lam, mode, path, _dptr(scratch),
+              scratch.numel(), _stream(stream))
 
 
 def vest_sweep_core(ix: Index, m: Model, reg: int, lam: float, scratch: torch.Tensor, stream=None):

@@ -57,3 +57,29 @@ def test_batched_replay_continues_and_matches_the_oracle_f64():
             O.sweep_factors(prob, om, reg, lam, -1)
             O.sweep_core(prob, om, reg, lam)
         assert model_err(job.model, om) < 1e-9, model_err(job.model, om)
+
+
+def test_autotuned_batch_equals_plain_with_the_same_choices():
+    """The autotuner sets one kernel per shape class; the batched form with those choices equals
+    the plain form with the same choices bitwise, and every job stays within FP32 rounding of the
+    library's default choice."""
+    specs = _specs(np.float32)
+    tuned = B.prepare(specs)
+    table = B.autotune(tuned, trials=1)
+    assert {B.shape_key(j) for j in tuned} == set(table)
+    assert all(v["path"] in (V.DELTA_FMA, V.DELTA_AUTO) for v in table.values())
+    plain = B.prepare(specs)
+    for j, t in zip(plain, tuned):
+        j.path = t.path
+    B.run_plain(plain, 3)
+    B.BatchedRun(tuned, 3, n_streams=4).replay()
+    default = B.prepare(specs)
+    B.run_plain(default, 3)
+    torch.cuda.synchronize()
+    for a, b, c in zip(plain, tuned, default):
+        fa, ca, _, _ = a.model.to_host()
+        fb, cb, _, _ = b.model.to_host()
+        fc, cc, _, _ = c.model.to_host()
+        assert all(np.array_equal(x, y) for x, y in zip(fa, fb)) and np.array_equal(ca, cb)
+        scale = max(float(np.abs(x).max()) for x in fc)
+        assert max(float(np.abs(x - y).max()) for x, y in zip(fa, fc)) <= 1e-3 * scale
