@@ -67,6 +67,10 @@ def parse():
                    help="after the timed steps, run vest_autosearch (Algorithm 2, VeST_auto) for up to this many "
                         "iterations from the initial model and report it")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--profile", default=None, choices=["sweep", "iteration"],
+                   help="run a short fixed sequence for an ncu capture instead of the benchmark: build the "
+                        "workload's index, then --steps factor sweeps of mode 0 (sweep) or --steps calls of "
+                        "vest_iteration with pr = 0.01 (iteration); no timing, no JSON line")
     p.add_argument("--start", default="init", choices=["init", "pruned"],
                    help="init: the U(0,1) start of Algorithm 2; pruned: 5 sweeps, then 90%% of every segment "
                         "pruned by responsibility (the sparse state where the HBM roofline applies)")
@@ -734,9 +738,38 @@ def main_sparsity_curve(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ profiling driver
+def main_profile(args):
+    """A short fixed sequence of library calls on the workload, for an ncu capture (the launches
+    to capture are selected with ncu's -k / -s / -c)."""
+    import torch
+
+    from paper_1904_02603_gb300 import build as Bd
+    from paper_1904_02603_gb300 import vest as V
+    torch.cuda.set_device(0)
+    Bd.build()
+    V.load()
+    w = datagen.WORKLOADS[args.workload]
+    reg = V.REG_LF if w.reg == "LF" else V.REG_L1
+    t, st, _ = datagen.make(w, device="cuda")
+    ix = V.vest_build_index(V.Tensor.from_host(t))
+    m = V.Model.from_host(st)
+    sc = V.make_scratch(ix, m)
+    for _ in range(args.steps):
+        if args.profile == "sweep":
+            V.vest_sweep_factors(ix, m, reg, w.lam, 0, sc)
+        else:
+            V.vest_iteration(ix, m, reg, w.lam, PRUNE_RATE, sc)
+    torch.cuda.synchronize()
+    print(f"profile run: {args.profile} x {args.steps} on {w.name}, device status {V.vest_device_status()}")
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
+    if args.profile:
+        main_profile(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

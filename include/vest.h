@@ -151,7 +151,8 @@ uint64_t vest_launch_count(void);
  * a healthy GPU never exhausts) abandons the rest of its work, raises a bit
  * here and returns, and the results of that call are not valid.  This call
  * synchronises the device, writes the bits raised since the last clear to
- * *flags (nullable; bit 0: a factor-sweep wait gave up), clears them when
+ * *flags (nullable; bit 0: a factor-sweep wait gave up, bit 1: a loss wait gave up
+ * -- the loss kernel behind vest_loss, vest_iteration and the core sweep), clears them when
  * clear != 0, and returns VEST_ERR_TIMEOUT when any was set, else VEST_OK. */
 vest_status vest_device_status(uint32_t* flags, int32_t clear);
 

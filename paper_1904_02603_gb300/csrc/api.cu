@@ -193,8 +193,10 @@ extern "C" {
 const char* vest_version(void) { return "vest-gb300 0.2 (sm_103a)"; }
 
 vest_status vest_device_status(uint32_t* flags, int32_t clear) {
-  uint32_t f = 0;
-  VEST_TRY(sweep_device_status(&f, clear != 0));
+  uint32_t f = 0, fl = 0;
+  VEST_TRY(sweep_device_status(&f, clear != 0));  // synchronises the device first
+  VEST_TRY(loss_device_status(&fl, clear != 0));
+  f |= fl;
   if (flags) *flags = f;
   if (f) return fail(VEST_ERR_TIMEOUT, "a bounded device wait gave up since the last clear (flags " + std::to_string(f) + ")");
   return VEST_OK;

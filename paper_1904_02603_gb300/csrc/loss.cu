@@ -8,12 +8,13 @@
 // blocks in a fixed order, so the loss is bitwise reproducible.
 #include <algorithm>
 
-#include "delta.cuh"
+#include "tc_delta.cuh"
 
 namespace vest {
 
 constexpr int kLossTask = 256;
 constexpr int kLossCtas = 760;  // fixed (sum order device-independent): one wave of 5 CTAs on 152 SMs
+constexpr int kLossTcCtas = 608;  // the tensor-core loss: one wave of 4 CTAs on 152 SMs, fixed likewise
 constexpr int kRegCtas = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -115,6 +116,117 @@ __global__ void __launch_bounds__(kLossTask / E, (delta_min_blocks<T, JN, JF, E>
   }
 }
 
+// The same loss with delta^(0) on the tensor cores (FP32 models the plan of tc_delta.cuh
+// serves, mode-0 rank <= 16): per task of 256 mode-0 CSR positions two groups of 128 entries,
+// each group's A rows written by their own lanes, the MMAs issued by one thread, delta read
+// back from the accumulator and dotted with the entry's mode-0 row.  Sums as in loss_kernel.
+// A wait that runs out marks the device status, abandons the CTA's entries and, after the
+// in-flight MMAs get the same bounded wait, frees tensor memory.
+static __device__ unsigned int g_loss_status;  // bit 1: an MMA completion wait gave up
+
+template <int JN, int NA>
+__global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
+    loss_tc_kernel(DevModel<float> M, DevMode<float> csr, const float* __restrict__ gp, LossArgs a, TcPlan tp,
+                   float* __restrict__ resid_csr0, float* __restrict__ resid_coo) {
+  constexpr int E = 2;
+  extern __shared__ __align__(128) unsigned char ltc_smem[];
+  __shared__ uint64_t mma_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int wait_failed;
+  __shared__ double red[32];
+  const ModeRoles& r = a.r;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  uint32_t* sBhi = reinterpret_cast<uint32_t*>(ltc_smem);
+  uint32_t* sBlo = reinterpret_cast<uint32_t*>(ltc_smem + tp.btile);
+  uint32_t* sAhi = reinterpret_cast<uint32_t*>(ltc_smem + 2 * tp.btile);
+  uint32_t* sAlo = reinterpret_cast<uint32_t*>(ltc_smem + 2 * tp.btile + tp.atile);
+  tc_fill_b<JN, NA>(sBhi, sBlo, gp, r, tp);
+  if (tid == 0) {
+    tc::mbar_init(&mma_bar, 1);
+    wait_failed = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(&tmem_slot, (uint32_t)tp.ncols);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = tmem_slot;
+  TcCta<NA> tcc;
+  tcc.init(tbase, tp, sBhi, sBlo, sAhi, sAlo);
+  uint32_t phase = 0;
+  const int64_t nnz = csr.nnz;
+  const int J0 = M.J[0];
+  float sq = 0.f, sqc = 0.f, xx = 0.f, xxc = 0.f;
+  auto kadd = [](float& s, float& c, float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  };
+  for (int64_t task = blockIdx.x; task < a.ntasks && !wait_failed; task += gridDim.x) {
+    const int64_t t0 = task * kLossTask;
+    const int cnt = (int)(min(t0 + (int64_t)kLossTask, nnz) - t0);
+    float a0[E][16], a1[E][NA == 2 ? 16 : 1], wr[E][16], am[E][16], xv[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int q = tid + e * 128;
+      const bool valid = q < cnt;
+      const int64_t p = t0 + (valid ? q : 0);
+      tc_row(a0[e], tp, M.A[r.f], csr.oidx[p], r.Jf, valid);
+      if constexpr (NA == 2) tc_row(a1[e], tp, M.A[r.slow[0]], csr.oidx[nnz + p], tp.JA1, valid);
+      if (tp.has_rest) {
+        tc_row(wr[e], tp, M.A[r.slow[NA - 1]], csr.oidx[(int64_t)NA * nnz + p], tp.O, valid);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) wr[e][i] = i == 0 ? 1.f : 0.f;
+      }
+      tc_row(am[e], tp, M.A[0], csr.nzrow[csr.rowk[p]], J0, valid);
+      xv[e] = valid ? csr.val[p] : 0.f;
+    }
+#pragma unroll
+    for (int g = 0; g < E; ++g) {
+      tcc.write_a(tid, a0[g], a1[g]);
+      __syncthreads();
+      if (tid == 0) tcc.issue(&mma_bar);
+      __syncwarp();
+      const bool done = tc::mbar_wait_bounded(&mma_bar, phase, kTcWaitPolls);
+      phase ^= 1u;
+      if (__any_sync(0xffffffffu, !done) && (tid & 31) == 0) wait_failed = 1;
+      tc::fence_after_sync();
+      float d[JN];
+      tcc.template delta<JN>(tp.Np, tp.O, wr[g], d);
+      tc::fence_before_sync();  // this group's accumulator reads before the next group's MMAs
+      const int q = tid + g * 128;
+      if (q < cnt) {
+        float b = 0.f;
+#pragma unroll
+        for (int j = 0; j < JN; ++j)
+          if (j < 16) b += am[g][j] * d[j];
+        const int64_t p = t0 + q;
+        const float res = xv[g] - b;
+        if (resid_csr0) resid_csr0[p] = res;
+        if (resid_coo) resid_coo[csr.perm[p]] = res;
+        kadd(sq, sqc, res * res);
+        kadd(xx, xxc, xv[g] * xv[g]);
+      }
+    }
+    __syncthreads();  // wait_failed is read uniformly by the loop condition
+  }
+  if (wait_failed) {
+    if (tid == 0) atomicOr(&g_loss_status, 2u);
+    tc::mbar_wait_bounded(&mma_bar, phase ^ 1u, kTcWaitPolls);
+  }
+  const double s1 = block_sum((double)sq - (double)sqc, red);
+  const double s2 = block_sum((double)xx - (double)xxc, red);
+  if (tid == 0) {
+    a.part[blockIdx.x * 2 + 0] = s1;
+    a.part[blockIdx.x * 2 + 1] = s2;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, (uint32_t)tp.ncols);
+}
+
 // regulariser partial sums over every factor and core element
 template <typename T>
 __global__ void reg_kernel(DevModel<T> M, int reg, double* __restrict__ part) {
@@ -181,6 +293,45 @@ static vest_status loss_nslow(int nslow, int Jf, const DevModel<T>& M, const Dev
   return launch_loss<T, JN, 0, -1, 1>(M, csr, gp, a, smem, grid, r0, rc, s);
 }
 
+template <int JN, int NA>
+static vest_status launch_loss_tc_jn(const DevModel<float>& M, const DevMode<float>& csr, const float* gp,
+                                     const LossArgs& a, const TcPlan& tp, int grid, float* r0, float* rc,
+                                     cudaStream_t s) {
+  TcPlan tpl = tp;
+  tpl.base8 = 1;
+  for (int k = 0; k < M.N; ++k)
+    if (reinterpret_cast<uintptr_t>(M.A[k]) % 8 != 0) tpl.base8 = 0;
+  size_t smem = 2 * tp.btile + tp.ubytes;
+  // no more CTAs on an SM than its 512 TMEM columns hold, so no allocation ever waits
+  smem = std::max(smem, (size_t)(228 * 1024) / (tp.per_sm + 1) - 1024 + 16);
+  auto kern = loss_tc_kernel<JN, NA>;
+  VEST_TRY(allow_smem(kern, smem));
+  kern<<<grid, 128, smem, s>>>(M, csr, gp, a, tpl, r0, rc);
+  VEST_LAUNCH("loss_tc_kernel");
+  return VEST_OK;
+}
+
+template <typename T>
+static vest_status launch_loss_tc(int JN, const DevModel<T>& M, const DevMode<T>& csr, const T* gp, const LossArgs& a,
+                                  const TcPlan& tp, int grid, T* r0, T* rc, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    const bool two = tp.na == 2;
+    switch (JN) {
+      case 4: return two ? launch_loss_tc_jn<4, 2>(M, csr, gp, a, tp, grid, r0, rc, s)
+                         : launch_loss_tc_jn<4, 1>(M, csr, gp, a, tp, grid, r0, rc, s);
+      case 8: return two ? launch_loss_tc_jn<8, 2>(M, csr, gp, a, tp, grid, r0, rc, s)
+                         : launch_loss_tc_jn<8, 1>(M, csr, gp, a, tp, grid, r0, rc, s);
+      case 10: return two ? launch_loss_tc_jn<10, 2>(M, csr, gp, a, tp, grid, r0, rc, s)
+                          : launch_loss_tc_jn<10, 1>(M, csr, gp, a, tp, grid, r0, rc, s);
+      case 12: return two ? launch_loss_tc_jn<12, 2>(M, csr, gp, a, tp, grid, r0, rc, s)
+                          : launch_loss_tc_jn<12, 1>(M, csr, gp, a, tp, grid, r0, rc, s);
+      default: return two ? launch_loss_tc_jn<16, 2>(M, csr, gp, a, tp, grid, r0, rc, s)
+                          : launch_loss_tc_jn<16, 1>(M, csr, gp, a, tp, grid, r0, rc, s);
+    }
+  }
+  return fail(VEST_ERR_UNSUPPORTED, "tensor-core loss needs an FP32 model");
+}
+
 template <typename T>
 vest_status loss_impl(const vest_index* ix, const vest_model* m, int reg, double lambda, double* out, T* resid_csr0,
                       T* resid_coo, char* scratch, const ScratchPlan& plan, cudaStream_t s) {
@@ -204,7 +355,19 @@ vest_status loss_impl(const vest_index* ix, const vest_model* m, int reg, double
   double* lpart = reinterpret_cast<double*>(scratch + plan.off_part);
   double* rpart = lpart + 2 * kLossCtas;
   a.part = lpart;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.ntasks, kLossCtas));
+  int grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.ntasks, kLossCtas));
+  TcPlan tp{};
+  if constexpr (sizeof(T) == 4) {
+    if (ix->nnz > 0 && JN <= 16 && tensor_cores_enabled() && tc_plan(r, M.N, JN, 0, &tp)) {
+      grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.ntasks, kLossTcCtas));
+      VEST_TRY(launch_loss_tc(JN, M, dev_mode<T>(ix, 0), gp, a, tp, grid, resid_csr0, resid_coo, s));
+      reg_kernel<T><<<kRegCtas, 256, 0, s>>>(M, reg, rpart);
+      VEST_LAUNCH("reg_kernel");
+      loss_final_kernel<<<1, 256, 0, s>>>(lpart, grid, rpart, kRegCtas, lambda, out);
+      VEST_LAUNCH("loss_final_kernel");
+      return VEST_OK;
+    }
+  }
   if (ix->nnz > 0) {
     const DevMode<T> csr = dev_mode<T>(ix, 0);
     switch (JN) {
@@ -224,6 +387,18 @@ vest_status loss_impl(const vest_index* ix, const vest_model* m, int reg, double
 }
 
 size_t loss_part_bytes() { return (size_t)(2 * kLossCtas + kRegCtas) * 8; }
+
+// Bits set by the tensor-core loss kernel since the last clear (bit 1: a bounded wait gave up).
+vest_status loss_device_status(uint32_t* flags, bool clear) {
+  unsigned int v = 0;
+  VEST_CUDA(cudaMemcpyFromSymbol(&v, g_loss_status, sizeof(v)));
+  if (clear && v) {
+    const unsigned int z = 0;
+    VEST_CUDA(cudaMemcpyToSymbol(g_loss_status, &z, sizeof(z)));
+  }
+  *flags = v;
+  return VEST_OK;
+}
 
 // Loss from per-CTA (sum r^2, sum x^2) partials already in the loss region (nl of them,
 // at most kLossCtas): adds the regulariser and writes the five loss values.

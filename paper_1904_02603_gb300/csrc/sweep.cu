@@ -24,8 +24,7 @@
 #include <algorithm>
 #include <cstdlib>
 
-#include "delta.cuh"
-#include "tcgen05.cuh"
+#include "tc_delta.cuh"
 
 namespace vest {
 
@@ -316,59 +315,25 @@ __global__ void __launch_bounds__(256 / E, (delta_min_blocks<T, JN, JF, E>(256 /
 }
 
 // ------------------------------------------------------------------ tensor-core delta (FP32)
-// Eq. 11 in two stages for each group of 128 entries (one entry per accumulator row):
-//   stage 1, tcgen05 MMA in split TF32 (hi*hi + hi*lo + lo*hi, about FP32 accuracy):
-//     T[e][(o, j)] = sum_k A[e][k] B[k][(o, j)], with A[e] the row of the other mode f
-//     (NA = 1) or the Khatri-Rao product of the rows of f and of the first slow mode
-//     (NA = 2), and B the core permuted to (k, (o, j_n)), o over the one remaining other
-//     mode (or a single o when none remains);
-//   stage 2, FP32 FMAs: delta_e(j) = sum_o w_e(o) T[e][(o, j)], w_e the row of the
-//     remaining mode (1 when none remains).
-// With the dense 10 x 10 x 10 core of the Zipf workload this moves 1000 of the 1100 FMAs
-// per entry of the staged contraction onto the tensor cores.  B sits in shared memory
-// (K-major, no swizzle) and the accumulator in tensor memory, column o * JN + j.  With one
-// A mode, A is written to shared memory by the lane of its entry (the MMA reads both
-// operands there; the region is reused for the staged vectors V once the task's last MMA
-// has completed), so the allocation is the accumulator alone: 128 columns for the Zipf
-// workload, four CTAs per SM.  With two A modes the wider A goes to tensor memory.  One
-// thread issues the MMAs and commits them to an mbarrier that every thread waits on with a
-// bounded number of polls; a wait that runs out marks the device status and ends the CTA's
-// work after its in-flight MMAs are given the same bounded wait.
-struct TcPlan {
-  int na;        // other modes folded into A: 1 (A in shared memory) or 2 (A in tensor memory)
-  int jf8;       // rank of mode f rounded up to 8: A columns per row of the second A mode
-  int JA1;       // rank of the second A mode (1 when na = 1)
-  int Kp;        // A width: jf8 * JA1, a multiple of 8 (the MMA's K step)
-  int O;         // rank of the remaining mode (1 when none)
-  int has_rest;  // a remaining mode exists
-  int Np;        // MMA N: O * JN rounded up to 16
-  int colD;      // first accumulator column: 0 (na = 1) or 2 Kp after A hi and lo (na = 2)
-  int ncols;     // TMEM columns allocated: power of two >= colD + Np
-  int per_sm;    // CTAs per SM that the allocation allows: 512 / ncols
-  size_t btile;  // bytes of one B tile (hi or lo): Np * Kp * 4
-  size_t atile;  // bytes of one A tile (hi or lo) in shared memory: 128 * Kp * 4 (0 when na = 2)
-  size_t ubytes; // shared region of A hi, A lo and, later, V: max(2 atile, V bytes), 128-aligned
-};
-
-constexpr uint32_t kTcWaitPolls = 1u << 22;  // bounded mbarrier wait (seconds at worst, never in practice)
-constexpr int kTcMaxChunks = 14;             // accumulator columns read in 16-column chunks: Np <= 224
+// The task kernel with phase 1 on the tensor cores (tc_delta.cuh): per task two groups of 128
+// entries, each group's A rows written by their own lanes, the MMAs issued by one thread,
+// stage 2 read back from the accumulator, then phases 2 and 3 as in sweep_task_kernel.  The
+// A region of shared memory takes the staged vectors V once the task's last MMA has completed.
+// A wait that runs out marks the device status and ends the CTA's work after its in-flight
+// MMAs are given the same bounded wait.
 static __device__ unsigned int g_sweep_status;  // bit 0: an MMA completion wait gave up
 
-// stage 2 for one lane: delta(j) += w(o) T[o * JN + j] over the accumulator's Np columns
-template <int JN>
-__device__ __forceinline__ void contract_rest(uint32_t taddr, int Np, int O, const float (&w)[16], float (&d)[JN]) {
+// One staged vector V of L floats (L even; its start is L * 4 * q bytes into a 16-byte aligned
+// array): 16-byte stores when L is a multiple of 4 (at L = 12 the 32 lanes' pieces then fill
+// whole wavefronts), 8-byte stores otherwise.
+template <int L>
+__device__ __forceinline__ void store_row(float* dst, const float (&v)[L]) {
+  if constexpr (L % 4 == 0) {
 #pragma unroll
-  for (int c = 0; c < kTcMaxChunks * 16; c += 16) {
-    if (c < Np) {
-      uint32_t u[16];
-      tc::ld16(taddr + (uint32_t)c, u);
-      tc::wait_ld();
+    for (int i = 0; i < L; i += 4) *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+  } else {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int col = c + i, o = col / JN, j = col - o * JN;
-        if (o < 16 && o < O) d[j] = fmaf(w[o], __uint_as_float(u[i]), d[j]);
-      }
-    }
+    for (int i = 0; i < L; i += 2) *reinterpret_cast<float2*>(dst + i) = make_float2(v[i], v[i + 1]);
   }
 }
 
@@ -396,23 +361,7 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
   const TaskSmem<T> ts =
       carve_task_smem<T>(tc_smem_raw, 2 * tp.btile + tp.ubytes, TASK, L, KMAX, P, NT, reinterpret_cast<T*>(U));
 
-  // B tiles from the permuted core gp[((o_full * Jf + cf) * JN + j]: element (n, k) with
-  // n = o * JN + j, k = s0 * jf8 + cf (s0 = 0 when na = 1), o_full = o (na = 1) or s0 + JA1 o
-  for (int e = tid; e < tp.Np * tp.Kp; e += blockDim.x) {
-    const int n = e / tp.Kp, k = e - n * tp.Kp;
-    const int o = n / JN, j = n - o * JN;
-    const int s0 = NA == 2 ? k / tp.jf8 : 0, cf = NA == 2 ? k - s0 * tp.jf8 : k;
-    float v = 0.f;
-    if (j < r.Jn && cf < r.Jf && o < tp.O && s0 < tp.JA1) {
-      const int64_t of = NA == 2 ? (int64_t)s0 + (int64_t)tp.JA1 * o : (int64_t)o;
-      v = gp[(of * r.Jf + cf) * JN + j];
-    }
-    uint32_t hi, lo;
-    tc::split_tf32(v, hi, lo);
-    const uint32_t wi = tc::kmajor_offset(n, k, tp.Kp) >> 2;
-    sBhi[wi] = hi;
-    sBlo[wi] = lo;
-  }
+  tc_fill_b<JN, NA>(sBhi, sBlo, gp, r, tp);
   for (int t = tid; t < NT; t += blockDim.x) sweep_tile(t, JN, r.Jn, MODE, ts.sCab[t], ts.sOut[t]);
   if (tid == 0) {
     tc::mbar_init(&mma_bar, 1);
@@ -424,12 +373,8 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = tmem_slot;
-  const uint32_t lane = (uint32_t)(32 * (warp & 3)) << 16;
-  const uint32_t colAlo = (uint32_t)tp.Kp, colD = (uint32_t)tp.colD;
-  const uint32_t idesc = tc::idesc_tf32(128, tp.Np);
-  const uint32_t sbo = (uint32_t)tp.Kp * 32u;
-  const uint32_t bhi_addr = tc::smem_u32(sBhi), blo_addr = tc::smem_u32(sBlo);
-  const uint32_t ahi_addr = tc::smem_u32(sAhi), alo_addr = tc::smem_u32(sAlo);
+  TcCta<NA> tcc;
+  tcc.init(tbase, tp, sBhi, sBlo, sAhi, sAlo);
   uint32_t phase = 0;
 
   const int64_t nnz = csr.nnz;
@@ -461,18 +406,10 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
       const int64_t p = g0 + (valid ? q : 0);
       rk[e] = csr.rowk[p];
       rkprev[e] = (valid && q > 0 && (q & 31) == 0) ? csr.rowk[p - 1] : rk[e];
-      const float* ra0 = M.A[r.f] + (int64_t)csr.oidx[p] * r.Jf;
-#pragma unroll
-      for (int i = 0; i < 16; ++i) a0[e][i] = (valid && i < r.Jf) ? __ldg(ra0 + i) : 0.f;
-      if constexpr (NA == 2) {
-        const float* ra1 = M.A[r.slow[0]] + (int64_t)csr.oidx[nnz + p] * tp.JA1;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) a1[e][i] = (valid && i < tp.JA1) ? __ldg(ra1 + i) : 0.f;
-      }
+      tc_row(a0[e], tp, M.A[r.f], csr.oidx[p], r.Jf, valid);
+      if constexpr (NA == 2) tc_row(a1[e], tp, M.A[r.slow[0]], csr.oidx[nnz + p], tp.JA1, valid);
       if (tp.has_rest) {
-        const float* rr = M.A[r.slow[NA - 1]] + (int64_t)csr.oidx[(int64_t)NA * nnz + p] * tp.O;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) wr[e][i] = (valid && i < tp.O) ? __ldg(rr + i) : 0.f;
+        tc_row(wr[e], tp, M.A[r.slow[NA - 1]], csr.oidx[(int64_t)NA * nnz + p], tp.O, valid);
       } else {
 #pragma unroll
         for (int i = 0; i < 16; ++i) wr[e][i] = i == 0 ? 1.f : 0.f;
@@ -494,71 +431,15 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
     float d[E][JN];
 #pragma unroll
     for (int g = 0; g < E; ++g) {
-      // A operand of this group's entry tid: hi and lo, in shared memory (na = 1, the row is
-      // the entry, 16-byte pieces of four k) or in this lane's tensor-memory row (na = 2)
-      if constexpr (NA == 1) {
-#pragma unroll
-        for (int c = 0; c < 16; c += 4) {
-          if (c < tp.Kp) {
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) tc::split_tf32(a0[g][c + i], h[i], l[i]);
-            const uint32_t wi = tc::kmajor_offset(tid, c, tp.Kp) >> 2;
-            *reinterpret_cast<uint4*>(sAhi + wi) = make_uint4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<uint4*>(sAlo + wi) = make_uint4(l[0], l[1], l[2], l[3]);
-          }
-        }
-        tc::fence_async_smem();
-      } else {
-#pragma unroll
-        for (int s0 = 0; s0 < 16; ++s0) {
-          if (s0 < tp.JA1) {
-            const float w0 = a1[g][s0];
-#pragma unroll
-            for (int c = 0; c < 16; c += 8) {
-              if (c < tp.jf8) {
-                uint32_t h[8], l[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) tc::split_tf32(a0[g][c + i] * w0, h[i], l[i]);
-                const uint32_t col = (uint32_t)(s0 * tp.jf8 + c);
-                tc::st8(tbase + lane + col, h);
-                tc::st8(tbase + lane + colAlo + col, l);
-              }
-            }
-          }
-        }
-        tc::wait_st();
-      }
-      tc::fence_before_sync();
+      tcc.write_a(tid, a0[g], a1[g]);
       __syncthreads();
-      if (tid == 0) {
-        tc::fence_after_sync();
-        for (int ks = 0; ks < tp.Kp / 8; ++ks) {
-          const uint64_t bh = tc::smem_desc(bhi_addr + (uint32_t)ks * 256u, 128u, sbo);
-          const uint64_t bl = tc::smem_desc(blo_addr + (uint32_t)ks * 256u, 128u, sbo);
-          if constexpr (NA == 1) {
-            const uint64_t ah = tc::smem_desc(ahi_addr + (uint32_t)ks * 256u, 128u, sbo);
-            const uint64_t al = tc::smem_desc(alo_addr + (uint32_t)ks * 256u, 128u, sbo);
-            tc::mma_tf32_ss(tbase + colD, ah, bh, idesc, ks > 0 ? 1u : 0u);
-            tc::mma_tf32_ss(tbase + colD, ah, bl, idesc, 1u);
-            tc::mma_tf32_ss(tbase + colD, al, bh, idesc, 1u);
-          } else {
-            tc::mma_tf32_ts(tbase + colD, tbase + ks * 8, bh, idesc, ks > 0 ? 1u : 0u);
-            tc::mma_tf32_ts(tbase + colD, tbase + ks * 8, bl, idesc, 1u);
-            tc::mma_tf32_ts(tbase + colD, tbase + colAlo + ks * 8, bh, idesc, 1u);
-          }
-        }
-        tc::mma_commit(&mma_bar);
-      }
+      if (tid == 0) tcc.issue(&mma_bar);
       __syncwarp();
       const bool done = tc::mbar_wait_bounded(&mma_bar, phase, kTcWaitPolls);
       phase ^= 1u;
       if (__any_sync(0xffffffffu, !done) && (tid & 31) == 0) wait_failed = 1;  // checked after the task's V barrier
       tc::fence_after_sync();
-      // stage 2: delta(j) = sum_o w(o) T[o * JN + j]
-#pragma unroll
-      for (int j = 0; j < JN; ++j) d[g][j] = 0.f;
-      contract_rest<JN>(tbase + lane + colD, tp.Np, tp.O, wr[g], d[g]);
+      tcc.template delta<JN>(tp.Np, tp.O, wr[g], d[g]);
       tc::fence_before_sync();  // this group's accumulator reads before the next group's MMAs
     }
     // every MMA of the task has completed (each thread waited): V may take over the A region
@@ -566,11 +447,12 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
     for (int g = 0; g < E; ++g) {
       const int q = tid + g * 128;
       if (q < cnt) {
-        T* dst = ts.sV + q * L;
+        float v[L];
 #pragma unroll
-        for (int j = 0; j < JN; ++j) dst[j] = d[g][j];
-        dst[JN] = xv[g];
-        dst[JN + 1] = T(0);
+        for (int j = 0; j < JN; ++j) v[j] = d[g][j];
+        v[JN] = xv[g];
+        v[JN + 1] = 0.f;
+        store_row<L>(ts.sV + q * L, v);
       }
     }
     // row table: sptr[k - k0] = start of every row that starts inside the task, sptr[0] and
@@ -647,12 +529,28 @@ __global__ void __launch_bounds__(256) sweep_fixup_kernel(DevModel<T> M, DevMode
   }
 }
 
-// Every non-empty row from its sums in the row buffer, one thread per row (FP64 CD).
+// Every non-empty row from its sums in the row buffer, one thread per row (FP64 CD).  A CTA
+// takes `rb` consecutive rows at a time: their sums are one contiguous run of the row buffer,
+// copied into shared memory with coalesced loads (odd row stride, so the threads' column reads
+// do not collide on banks) before each thread finishes its row from there.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(128) finish_rows_kernel(DevModel<T> M, DevMode<T> csr, SweepArgs a) {
+__global__ void __launch_bounds__(128) finish_rows_kernel(DevModel<T> M, DevMode<T> csr, SweepArgs a, int rb) {
+  extern __shared__ __align__(16) unsigned char fr_smem[];
+  T* sb = reinterpret_cast<T*>(fr_smem);
+  const int P = a.P, PS = P | 1;
   const int64_t R = *csr.nnzrows;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < R; k += (int64_t)gridDim.x * blockDim.x)
-    finish_row<T, T, MODE>(M, a.r.n, (int64_t)csr.nzrow[k], a.rowbuf_t<T>() + (size_t)k * a.P, a);
+  for (int64_t k0 = (int64_t)blockIdx.x * rb; k0 < R; k0 += (int64_t)gridDim.x * rb) {
+    const int nrow = (int)min((int64_t)rb, R - k0);
+    const T* src = a.rowbuf_t<T>() + (size_t)k0 * P;
+    for (int i = threadIdx.x; i < nrow * P; i += blockDim.x) {
+      const int rr = i / P;
+      sb[rr * PS + (i - rr * P)] = src[i];
+    }
+    __syncthreads();
+    for (int rr = threadIdx.x; rr < nrow; rr += blockDim.x)
+      finish_row<T, T, MODE>(M, a.r.n, (int64_t)csr.nzrow[k0 + rr], sb + (size_t)rr * PS, a);
+    __syncthreads();
+  }
 }
 
 // Rows with no observed entry: the update gives 0; their Delta is 0.
@@ -761,57 +659,6 @@ static vest_status dispatch_jn(int JN, int nslow, int Jf, const DevModel<T>& M, 
 }
 
 // ------------------------------------------------------------------ tensor-core path selection
-// The tensor-core delta serves FP32 models whose other modes split into one or two A modes
-// (ranks <= 16) and at most one remaining mode (rank <= 16), with 2 Kp + Np <= 256 TMEM
-// columns.  Among the feasible splits the one with the least CUDA-core work per entry is
-// taken: stage 2's O * JN FMAs plus the A split (and, with two A modes, their products).
-// VEST_TENSOR_CORES=0 in the environment selects the FMA kernels everywhere.
-static bool tensor_cores_enabled() {
-  static const bool on = [] {
-    const char* v = std::getenv("VEST_TENSOR_CORES");
-    return !(v && v[0] == '0');
-  }();
-  return on;
-}
-
-static bool tc_plan(const ModeRoles& r, int order, int JN, TcPlan* out) {
-  int best = 1 << 30;
-  bool found = false;
-  for (int na = 1; na <= 2; ++na) {
-    const int nother = order - 1;
-    if (na > nother) break;
-    const int nrest = nother - na;
-    if (nrest > 1) continue;
-    const int ja1 = na == 2 ? r.Js[0] : 1;
-    const int jr = nrest ? r.Js[na - 1] : 1;
-    if (r.Jf > 16 || ja1 > 16 || jr > 16) continue;
-    TcPlan p{};
-    p.na = na;
-    p.jf8 = (r.Jf + 7) / 8 * 8;
-    p.JA1 = ja1;
-    p.Kp = p.jf8 * ja1;
-    p.O = jr;
-    p.has_rest = nrest;
-    p.Np = (jr * JN + 15) / 16 * 16;
-    if (p.Np > kTcMaxChunks * 16) continue;
-    p.colD = na == 1 ? 0 : 2 * p.Kp;
-    if (p.colD + p.Np > 256) continue;
-    p.ncols = 32;
-    while (p.ncols < p.colD + p.Np) p.ncols *= 2;
-    p.per_sm = 512 / p.ncols;
-    p.btile = (size_t)p.Np * p.Kp * 4;
-    p.atile = na == 1 ? (size_t)128 * p.Kp * 4 : 0;
-    p.ubytes = align_up(std::max(2 * p.atile, (size_t)kTask * (JN + 2) * 4), 128);
-    const int cost = jr * JN + (na == 2 ? 3 : 2) * p.Kp;
-    if (cost < best) {
-      best = cost;
-      *out = p;
-      found = true;
-    }
-  }
-  return found;
-}
-
 template <int JN, int MODE>
 static vest_status launch_tc(const DevModel<float>& M, const DevMode<float>& csr, const float* gp, SweepArgs a,
                              const TcPlan& tp, cudaStream_t s) {
@@ -821,9 +668,13 @@ static vest_status launch_tc(const DevModel<float>& M, const DevMode<float>& csr
   const size_t sm_bytes = 228 * 1024, reserved = 1024;
   smem = std::max(smem, sm_bytes / (tp.per_sm + 1) - reserved + 16);
   if (smem > kSmemMax) return fail(VEST_ERR_UNSUPPORTED, "tensor-core factor sweep: shared memory exceeds 227 KB");
+  TcPlan tpl = tp;
+  tpl.base8 = 1;
+  for (int k = 0; k < M.N; ++k)
+    if (reinterpret_cast<uintptr_t>(M.A[k]) % 8 != 0) tpl.base8 = 0;
   auto kern = tp.na == 2 ? sweep_task_tc_kernel<JN, MODE, 2> : sweep_task_tc_kernel<JN, MODE, 1>;
   VEST_TRY(allow_smem(kern, smem));
-  kern<<<(unsigned)ceil_div(a.ntasks, a.tpc), 128, smem, s>>>(M, csr, gp, a, tp);
+  kern<<<(unsigned)ceil_div(a.ntasks, a.tpc), 128, smem, s>>>(M, csr, gp, a, tpl);
   VEST_LAUNCH("sweep_task_tc_kernel");
   return VEST_OK;
 }
@@ -885,7 +736,7 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
   TcPlan tp{};
   const bool use_tc = sizeof(T) == 4 && a.task == 256 &&
                       (a.path == VEST_DELTA_TENSOR || (a.path == VEST_DELTA_AUTO && tensor_cores_enabled())) &&
-                      tc_plan(r, M.N, JN, &tp);
+                      tc_plan(r, M.N, JN, (size_t)kTask * (JN + 2) * 4, &tp);
   if constexpr (sizeof(T) == 4) {
     if (use_tc) VEST_TRY(dispatch_tc<MODE>(JN, M, csr, gp, a, tp, s));
     else VEST_TRY(dispatch_jn<T, MODE>(JN, r.nslow, r.Jf, M, csr, gp, a, smem, s));
@@ -898,8 +749,12 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
   const int64_t fgrid = std::min<int64_t>(nblocks, (int64_t)num_sms() * 8);
   fk<<<(unsigned)fgrid, 256, fsmem, s>>>(M, csr, a, (int)nblocks);
   VEST_LAUNCH("sweep_fixup_kernel");
-  const int64_t rgrid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->mode[n].cap, 128), (int64_t)num_sms() * 8));
-  finish_rows_kernel<T, MODE><<<(unsigned)rgrid, 128, 0, s>>>(M, csr, a);
+  const int fps = a.P | 1;
+  const int rb = (int)std::max<size_t>(1, std::min<size_t>(128, (size_t)(48 * 1024) / ((size_t)fps * sizeof(T))));
+  const size_t rsm = (size_t)rb * fps * sizeof(T);
+  const int64_t rgrid2 = std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->mode[n].cap, rb), (int64_t)num_sms() * 8));
+  VEST_TRY(allow_smem(finish_rows_kernel<T, MODE>, rsm));
+  finish_rows_kernel<T, MODE><<<(unsigned)rgrid2, 128, rsm, s>>>(M, csr, a, rb);
   VEST_LAUNCH("finish_rows_kernel");
   return VEST_OK;
 }
@@ -936,7 +791,7 @@ bool sweep_tc_applies(const vest_model* m, int n) {
   if (m->dtype != VEST_F32) return false;
   const ModeRoles r = mode_roles(m->ranks, m->order, n);
   TcPlan tp{};
-  return tc_plan(r, m->order, jn_bucket(r.Jn), &tp);
+  return tc_plan(r, m->order, jn_bucket(r.Jn), (size_t)kTask * (jn_bucket(r.Jn) + 2) * 4, &tp);
 }
 
 // Bits set by the factor-sweep kernels since the last clear (bit 0: a bounded wait on the

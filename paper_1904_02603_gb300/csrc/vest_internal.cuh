@@ -187,6 +187,8 @@ size_t radix_hist_elems(int64_t n);
 // Status bits the factor-sweep kernels raise instead of trapping (bit 0: a bounded wait
 // on the tensor cores gave up); reads them after a device synchronise, clears on request.
 vest_status sweep_device_status(uint32_t* flags, bool clear);
+// The same for the tensor-core loss kernel (bit 1); no synchronise of its own.
+vest_status loss_device_status(uint32_t* flags, bool clear);
 
 // Whether the tensor-core delta of the FP32 factor sweep serves mode n of this model.
 bool sweep_tc_applies(const vest_model* m, int n);

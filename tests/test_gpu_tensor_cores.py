@@ -40,6 +40,9 @@ TC_CASES = {
     "n2_rank9": dict(dims=(700, 500), ranks=(9, 6), nnz=20000),  # no remaining mode
     "n4_mixed": dict(dims=(30, 25, 20, 15), ranks=(5, 6, 7, 3), nnz=6000),
     "n3_tail": dict(dims=(50, 40, 30), ranks=(6, 5, 4), nnz=257),  # one full task and one entry
+    # a rank above 16: no padded factor copies, so mode 0 (bucket 32) reads the caller's rows,
+    # of odd length (7 and 5), one element at a time; modes 1 and 2 take the FMA kernels
+    "n3_rank20_odd": dict(dims=(60, 50, 40), ranks=(20, 7, 5), nnz=7000),
 }
 
 
@@ -144,3 +147,21 @@ def test_tensor_core_and_fma_paths_agree_but_differ():
     tcs = [f.cpu().numpy() for f in mdl.factors]
     assert max(rel_err(a, b) for a, b in zip(tcs, fma)) < TOL
     assert any(not np.array_equal(a, b) for a, b in zip(tcs, fma))
+
+
+@pytest.mark.parametrize("name", sorted(TC_CASES))
+def test_tensor_core_loss_matches_oracle(name):
+    """vest_loss on an FP32 model takes the tensor-core loss kernel (delta^(0) by the MMA, dotted
+    with the mode-0 row): the residuals (Eq. 7) and the five loss values against the oracle."""
+    t, st = _case(name, masked=True)
+    ten, mdl = _device(t, st)
+    ix = V.vest_build_index(ten)
+    sc = V.make_scratch(ix, mdl)
+    resid = torch.empty(t.nnz, dtype=torch.float32, device="cuda")
+    out = V.vest_loss(ix, mdl, V.REG_L1, 0.05, sc, resid=resid).cpu().numpy()
+    prob, om = oracle_pair(t, st.astype(np.float32).astype(np.float64))
+    ref = O.loss(prob, om, O.REG_L1, 0.05)
+    r_ref = prob.x - O.reconstruct(prob, om)
+    assert rel_err(resid.cpu().numpy(), r_ref) < TOL, name
+    assert np.all(np.abs(out - ref) <= TOL * np.abs(ref)), (out, ref)
+    assert V.vest_device_status() == 0
