@@ -354,10 +354,30 @@ __global__ void core_gram_merge_kernel(const double* __restrict__ part, int kspl
 }
 
 // ================================================================== g pass (one block)
+// v[q] = row[q] for q < len (len <= kCoreMaxM), 0 beyond.  In pairs when `pair` is set: the
+// row start is 2-element aligned and, for odd len, the row goes on past row[len - 1].
+template <typename T>
+__device__ __forceinline__ void row_part(const T* row, int len, int pair, T (&v)[kCoreMaxM]) {
+  if (pair) {
+#pragma unroll
+    for (int q = 0; q < kCoreMaxM; q += 2)
+      if (q < len) load2<T>(row + q, v[q], v[q + 1]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < kCoreMaxM; ++q)
+      if (q < len) v[q] = row[q];
+  }
+#pragma unroll
+  for (int q = 0; q < kCoreMaxM; ++q)
+    if (q >= len) v[q] = T(0);
+}
+
 struct GPassArgs {
   int J0, J1;
   CoreBlock cur, prev;
   int has_prev;
+  int pair_a1;  // mode-1 rows read two elements at a time (J1, both q0 even; aligned factor)
+  int pair_u;   // u rows read two elements at a time (aligned U)
   int64_t nnz;
   double* part;  // [ctas][b]
 };
@@ -396,7 +416,10 @@ __global__ void core_a0c_kernel(DevModel<T> M, const int32_t* __restrict__ nzrow
 // elements l, l + 32, ...; Kahan across heads).  g is linear in the rows, so row
 // segments cut by chunk edges need no fix-up.  All gathers of a chunk (a1, the
 // suffix weights, u, and the head lanes' a0 rows from A0c) are issued together
-// after the coalesced index loads.
+// after the coalesced index loads; a1 and u rows are read in pairs where aligned.
+// The pass is bound by the L1 data pipe, so a chunk of one row only (most chunks:
+// about 1.3 rows per chunk on the Zipf workload) sums h by reduce-scatter, 17
+// shuffles, instead of the segmented scan's 5 (m + 1).
 template <typename T>
 __global__ void __launch_bounds__(256, 3) core_g_pass_kernel(DevModel<T> M, DevMode<T> csr, T* r, const T* __restrict__ U,
                                                           const T* __restrict__ A0c, GPassArgs a) {
@@ -449,18 +472,34 @@ __global__ void __launch_bounds__(256, 3) core_g_pass_kernel(DevModel<T> M, DevM
       const T* a1 = M.A[1] + (int64_t)i1 * a.J1;
       T rv = rv0;
       T v[kCoreMaxM];
-#pragma unroll
-      for (int q = 0; q < kCoreMaxM; ++q)
-        if (q < m) v[q] = a1[a.cur.q0 + q];
+      row_part<T>(a1 + a.cur.q0, m, a.pair_a1, v);
       if (a.has_prev) {
         T cp;
         if (n3) cp = M.A[2][(int64_t)i2 * M.J[2] + a.prev.s];
         else suffix_weights<T>(M, csr.oidx, a.nnz, p, a.prev.s, 1, &cp, 1);
         const T* u = U + (int64_t)k * kCoreMaxM;
         T acc = T(0);
+        if (same_q) {
+          if (a.pair_u) {
 #pragma unroll
-        for (int q = 0; q < kCoreMaxM; ++q)
-          if (q < mp) acc += (same_q ? v[q] : a1[a.prev.q0 + q]) * u[q];
+            for (int q = 0; q < kCoreMaxM; q += 2)
+              if (q < mp) {
+                T u0, u1;
+                load2<T>(u + q, u0, u1);
+                acc += v[q] * u0;
+                if (q + 1 < mp) acc += v[q + 1] * u1;
+              }
+          } else {
+#pragma unroll
+            for (int q = 0; q < kCoreMaxM; ++q)
+              if (q < mp) acc += v[q] * u[q];
+          }
+        } else {
+          const T* w = a1 + a.prev.q0;
+#pragma unroll
+          for (int q = 0; q < kCoreMaxM; ++q)
+            if (q < mp) acc += w[q] * u[q];
+        }
         rv -= cp * acc;
         r[p] = rv;
       }
@@ -472,14 +511,49 @@ __global__ void __launch_bounds__(256, 3) core_g_pass_kernel(DevModel<T> M, DevM
       for (int q = 0; q < kCoreMaxM; ++q)
         if (q < m) h[q] = rc * v[q];
     }
+    if (__all_sync(0xffffffffu, k == __shfl_sync(0xffffffffu, k, 0))) {
+      // one row: reduce-scatter of the 10 sums (halves at offset 16, 3 | 2 at offset 8,
+      // butterfly over the last 3 at offsets 4, 2, 1); lanes 0, 8, 16, 24 hold q 0-2,
+      // 3-4, 5-7, 8-9
+      static_assert(kCoreMaxM == 10, "reduce-scatter split is written for 10 sums");
+      const bool up = lane & 16, b3 = lane & 8;
+      T k1[5], k2[3];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) k1[i] = (up ? h[i + 5] : h[i]) + __shfl_xor_sync(0xffffffffu, up ? h[i] : h[i + 5], 16);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const T hi = i < 2 ? k1[3 + i] : T(0);
+        k2[i] = (b3 ? hi : k1[i]) + __shfl_xor_sync(0xffffffffu, b3 ? k1[i] : hi, 8);
+      }
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) k2[i] += __shfl_xor_sync(0xffffffffu, k2[i], o);
+      if ((lane & 7) == 0) {
+        const int qb = (up ? 5 : 0) + (b3 ? 3 : 0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          if (i < (b3 ? 2 : 3)) sh[warp][qb + i] = k2[i];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int e = lane + 32 * i;
+        if (e < b) CoreAcc<T>::add(as[i], ac[i], sa[e % J0] * sh[warp][e / J0]);
+      }
+      __syncwarp();
+      continue;
+    }
     // segmented suffix sums: lane l ends with the sum over its row from l to the chunk end
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int ko = __shfl_down_sync(0xffffffffu, k, o);
 #pragma unroll
       for (int q = 0; q < kCoreMaxM; ++q) {
-        const T v = __shfl_down_sync(0xffffffffu, h[q], o);
-        if (lane + o < 32 && ko == k) h[q] += v;
+        if (q < m) {
+          const T v = __shfl_down_sync(0xffffffffu, h[q], o);
+          if (lane + o < 32 && ko == k) h[q] += v;
+        }
       }
     }
     unsigned heads = __ballot_sync(0xffffffffu, head);
@@ -1158,6 +1232,7 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
   // the per-piece gram region is free again: u and the a0 row per non-empty row
   T* U = reinterpret_cast<T*>(bf.Y);
   T* A0c = U + (size_t)(ix->mode[0].cap + 1) * kCoreMaxM;
+  a.pair_u = reinterpret_cast<uintptr_t>(U) % (2 * sizeof(T)) == 0;
   const int nctas_g = kGPassCtas;
   const size_t gsm = (size_t)8 * 32 * c.J0 * sizeof(T);
   if (ix->nnz > 0) {
@@ -1175,6 +1250,8 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
       blk.b = c.J0 * blk.m;
       a.cur = blk;
       a.has_prev = iblk > 0;
+      a.pair_a1 = c.J1 % 2 == 0 && blk.q0 % 2 == 0 && (!a.has_prev || a.prev.q0 % 2 == 0) &&
+                  reinterpret_cast<uintptr_t>(M.A[1]) % (2 * sizeof(T)) == 0;
       if (ix->nnz > 0) {
         if (a.has_prev) {
           core_u_kernel<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->mode[0].cap, 256), num_sms() * 4)),

@@ -163,15 +163,17 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
     c = (t - s) - y;
     s = t;
   };
-  for (int64_t task = blockIdx.x; task < a.ntasks && !wait_failed; task += gridDim.x) {
-    const int64_t t0 = task * kLossTask;
-    const int cnt = (int)(min(t0 + (int64_t)kLossTask, nnz) - t0);
-    float a0[E][16], a1[E][NA == 2 ? 16 : 1], wr[E][16], am[E][16], xv[E];
+  // gathers of both entries of the thread in task tk; the next task's are issued once the
+  // current one's rows are used, so their latency overlaps the current task's MMAs and sums
+  float a0[E][16], a1[E][NA == 2 ? 16 : 1], wr[E][16], am[E][16], xv[E];
+  auto gather = [&](int64_t tk) {
+    const int64_t g0 = tk * kLossTask;
+    const int gcnt = (int)(min(g0 + (int64_t)kLossTask, nnz) - g0);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int q = tid + e * 128;
-      const bool valid = q < cnt;
-      const int64_t p = t0 + (valid ? q : 0);
+      const bool valid = q < gcnt;
+      const int64_t p = g0 + (valid ? q : 0);
       tc_row(a0[e], tp, M.A[r.f], csr.oidx[p], r.Jf, valid);
       if constexpr (NA == 2) tc_row(a1[e], tp, M.A[r.slow[0]], csr.oidx[nnz + p], tp.JA1, valid);
       if (tp.has_rest) {
@@ -183,6 +185,12 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
       tc_row(am[e], tp, M.A[0], csr.nzrow[csr.rowk[p]], J0, valid);
       xv[e] = valid ? csr.val[p] : 0.f;
     }
+  };
+  if ((int64_t)blockIdx.x < a.ntasks) gather(blockIdx.x);
+  for (int64_t task = blockIdx.x; task < a.ntasks && !wait_failed; task += gridDim.x) {
+    const int64_t t0 = task * kLossTask;
+    const int cnt = (int)(min(t0 + (int64_t)kLossTask, nnz) - t0);
+    float res[E];
 #pragma unroll
     for (int g = 0; g < E; ++g) {
       tcc.write_a(tid, a0[g], a1[g]);
@@ -196,20 +204,24 @@ __global__ void __launch_bounds__(128, NA == 1 ? 4 : 2)
       float d[JN];
       tcc.template delta<JN>(tp.Np, tp.O, wr[g], d);
       tc::fence_before_sync();  // this group's accumulator reads before the next group's MMAs
+      float b = 0.f;
+#pragma unroll
+      for (int j = 0; j < JN; ++j)
+        if (j < 16) b += am[g][j] * d[j];
+      res[g] = xv[g] - b;
+    }
+#pragma unroll
+    for (int g = 0; g < E; ++g) {
       const int q = tid + g * 128;
       if (q < cnt) {
-        float b = 0.f;
-#pragma unroll
-        for (int j = 0; j < JN; ++j)
-          if (j < 16) b += am[g][j] * d[j];
         const int64_t p = t0 + q;
-        const float res = xv[g] - b;
-        if (resid_csr0) resid_csr0[p] = res;
-        if (resid_coo) resid_coo[csr.perm[p]] = res;
-        kadd(sq, sqc, res * res);
+        if (resid_csr0) resid_csr0[p] = res[g];
+        if (resid_coo) resid_coo[csr.perm[p]] = res[g];
+        kadd(sq, sqc, res[g] * res[g]);
         kadd(xx, xxc, xv[g] * xv[g]);
       }
     }
+    if (task + gridDim.x < a.ntasks) gather(task + gridDim.x);
     __syncthreads();  // wait_failed is read uniformly by the loop condition
   }
   if (wait_failed) {

@@ -529,28 +529,12 @@ __global__ void __launch_bounds__(256) sweep_fixup_kernel(DevModel<T> M, DevMode
   }
 }
 
-// Every non-empty row from its sums in the row buffer, one thread per row (FP64 CD).  A CTA
-// takes `rb` consecutive rows at a time: their sums are one contiguous run of the row buffer,
-// copied into shared memory with coalesced loads (odd row stride, so the threads' column reads
-// do not collide on banks) before each thread finishes its row from there.
+// Every non-empty row from its sums in the row buffer, one thread per row (FP64 CD).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(128) finish_rows_kernel(DevModel<T> M, DevMode<T> csr, SweepArgs a, int rb) {
-  extern __shared__ __align__(16) unsigned char fr_smem[];
-  T* sb = reinterpret_cast<T*>(fr_smem);
-  const int P = a.P, PS = P | 1;
+__global__ void __launch_bounds__(128) finish_rows_kernel(DevModel<T> M, DevMode<T> csr, SweepArgs a) {
   const int64_t R = *csr.nnzrows;
-  for (int64_t k0 = (int64_t)blockIdx.x * rb; k0 < R; k0 += (int64_t)gridDim.x * rb) {
-    const int nrow = (int)min((int64_t)rb, R - k0);
-    const T* src = a.rowbuf_t<T>() + (size_t)k0 * P;
-    for (int i = threadIdx.x; i < nrow * P; i += blockDim.x) {
-      const int rr = i / P;
-      sb[rr * PS + (i - rr * P)] = src[i];
-    }
-    __syncthreads();
-    for (int rr = threadIdx.x; rr < nrow; rr += blockDim.x)
-      finish_row<T, T, MODE>(M, a.r.n, (int64_t)csr.nzrow[k0 + rr], sb + (size_t)rr * PS, a);
-    __syncthreads();
-  }
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < R; k += (int64_t)gridDim.x * blockDim.x)
+    finish_row<T, T, MODE>(M, a.r.n, (int64_t)csr.nzrow[k], a.rowbuf_t<T>() + (size_t)k * a.P, a);
 }
 
 // Rows with no observed entry: the update gives 0; their Delta is 0.
@@ -749,12 +733,8 @@ static vest_status run_mode(const vest_index* ix, const DevModel<T>& M, int n, S
   const int64_t fgrid = std::min<int64_t>(nblocks, (int64_t)num_sms() * 8);
   fk<<<(unsigned)fgrid, 256, fsmem, s>>>(M, csr, a, (int)nblocks);
   VEST_LAUNCH("sweep_fixup_kernel");
-  const int fps = a.P | 1;
-  const int rb = (int)std::max<size_t>(1, std::min<size_t>(128, (size_t)(48 * 1024) / ((size_t)fps * sizeof(T))));
-  const size_t rsm = (size_t)rb * fps * sizeof(T);
-  const int64_t rgrid2 = std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->mode[n].cap, rb), (int64_t)num_sms() * 8));
-  VEST_TRY(allow_smem(finish_rows_kernel<T, MODE>, rsm));
-  finish_rows_kernel<T, MODE><<<(unsigned)rgrid2, 128, rsm, s>>>(M, csr, a, rb);
+  const int64_t rgrid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->mode[n].cap, 128), (int64_t)num_sms() * 8));
+  finish_rows_kernel<T, MODE><<<(unsigned)rgrid, 128, 0, s>>>(M, csr, a);
   VEST_LAUNCH("finish_rows_kernel");
   return VEST_OK;
 }
