@@ -36,10 +36,11 @@ constexpr int kCoreMaxB = 128;
 constexpr int kCoreMaxM = 10;
 constexpr int kGramKSplit = 64;     // fixed: reduction order does not depend on the device
 // Fixed CTA counts (the order of every sum is then the same on any device), chosen as
-// whole waves on 152 SMs: the stats pass holds 2 CTAs per SM (1216 = 4 waves), the g pass 3
-// (1368 = 3 waves).
-constexpr int kCorePassCtas = 1216;
-constexpr int kGPassCtas = 1368;
+// whole waves on 152 SMs: the stats pass holds 2 CTAs per SM (304 = one wave; each CTA ends
+// with an FP64 combination of its warps, which issues at the FP64 rate, so fewer CTAs pay it
+// fewer times), the g pass 4 (608 = one wave of grid-strided CTAs; 64 registers a thread).
+constexpr int kCorePassCtas = 304;
+constexpr int kGPassCtas = 608;
 
 struct CoreBlock {
   int64_t s;  // suffix linear index over modes >= 2
@@ -116,6 +117,29 @@ __device__ __forceinline__ void suffix_weights(const DevModel<T>& M, const int32
   }
 }
 
+// dst[i] = src[i] for i < len: 8- or 16-byte pair loads where `pair` says src is 2-element
+// aligned, a scalar tail for odd len.  The staging loops of the Gram and stats passes gather
+// whole factor rows this way: the gathers, not the arithmetic, fill the L1 data pipe there.
+template <typename T>
+__device__ __forceinline__ void copy_row(const T* __restrict__ src, int len, bool pair, T* dst) {
+  int q = 0;
+  if (pair) {
+    for (; q + 1 < len; q += 2) {
+      T x, y;
+      load2<T>(src + q, x, y);
+      dst[q] = x;
+      dst[q + 1] = y;
+    }
+  }
+  for (; q < len; ++q) dst[q] = src[q];
+}
+
+// Whether rows of A^(n) starting at column c0 are 2-element aligned for copy_row.
+template <typename T>
+__device__ __forceinline__ bool rows_paired(const DevModel<T>& M, int n, int64_t c0) {
+  return M.J[n] % 2 == 0 && c0 % 2 == 0 && reinterpret_cast<uintptr_t>(M.A[n]) % (2 * sizeof(T)) == 0;
+}
+
 // ================================================================== gram pass
 constexpr int kGramSgB = 16;  // suffixes per gram group at most (registers per lane: 2 x 16)
 
@@ -161,6 +185,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) core_gram_pass_ke
     qb[i] = y;
   }
   T acc[2][SGB];
+  const bool pair1 = rows_paired(M, 1, a.q0), pair2 = M.N == 3 && rows_paired(M, 2, a.s0);
   auto flush = [&](int64_t slot, int row) {
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -180,11 +205,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) core_gram_pass_ke
       if (p < t1) {
         sk[lane] = csr.rowk[p];
         T* se = st + lane * ld;
-        suffix_weights<T>(M, csr.oidx, a.nnz, p, a.s0, Sg, se, 1);
+        if (M.N == 3) copy_row<T>(M.A[2] + (int64_t)csr.oidx[a.nnz + p] * M.J[2] + a.s0, Sg, pair2, se);
+        else suffix_weights<T>(M, csr.oidx, a.nnz, p, a.s0, Sg, se, 1);
         for (int s = 0; s < Sg; ++s) se[s] *= se[s];
         for (int s = Sg; s < SGB; ++s) se[s] = T(0);
-        const T* a1 = M.A[1] + (int64_t)csr.oidx[p] * a.J1 + a.q0;
-        for (int q = 0; q < mq; ++q) se[SGB + q] = a1[q];
+        copy_row<T>(M.A[1] + (int64_t)csr.oidx[p] * a.J1 + a.q0, mq, pair1, se + SGB);
       }
       __syncwarp();
       const int n = (int)min((int64_t)32, t1 - c0);
@@ -333,10 +358,13 @@ __global__ void __launch_bounds__(256, 2) core_gram_gemm_kernel(GemmArgs a) {
     }
 }
 
-// Packed M of block (s0 + sidx, q chunk) in FP64 from the split partials.
+// Packed M of block (s0 + sidx, q chunk qc) in FP64 from the split partials; sidx = blockIdx.y,
+// so one launch merges every suffix of the group.
 __global__ void core_gram_merge_kernel(const double* __restrict__ part, int ksplit, int nX, int P, int J0, int mq,
-                                       int nY, int sidx, double* __restrict__ gram) {
+                                       int nY, int64_t s0, int nq0, int qc, int64_t nmmax, double* __restrict__ gram_all) {
   const int b = J0 * mq, nm = b * (b + 1) / 2;
+  const int sidx = blockIdx.y;
+  double* gram = gram_all + ((s0 + sidx) * nq0 + qc) * nmmax;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nm; e += gridDim.x * blockDim.x) {
     int k, l;
     entry_kl(e, b, k, l);
@@ -386,15 +414,17 @@ struct GPassArgs {
 template <typename T>
 __global__ void core_u_kernel(DevModel<T> M, const int32_t* __restrict__ nzrow, const int32_t* __restrict__ nnzrows,
                               const double* __restrict__ dprev, int J0, int mp, T* __restrict__ U) {
-  __shared__ double sd[kCoreMaxB];
-  for (int i = threadIdx.x; i < J0 * mp; i += blockDim.x) sd[i] = dprev[i];
+  // Delta in the storage type, converted once here rather than once per product (a conversion
+  // from FP64 issues at the FP64 rate)
+  __shared__ T sd[kCoreMaxB];
+  for (int i = threadIdx.x; i < J0 * mp; i += blockDim.x) sd[i] = (T)dprev[i];
   __syncthreads();
   const int64_t R = *nnzrows;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < R; k += (int64_t)gridDim.x * blockDim.x) {
     const T* a0 = M.A[0] + (int64_t)nzrow[k] * J0;
     for (int q = 0; q < mp; ++q) {
       T u = T(0);
-      for (int j = 0; j < J0; ++j) u += (T)sd[q * J0 + j] * a0[j];
+      for (int j = 0; j < J0; ++j) u += sd[q * J0 + j] * a0[j];
       U[k * kCoreMaxM + q] = u;
     }
   }
@@ -421,7 +451,7 @@ __global__ void core_a0c_kernel(DevModel<T> M, const int32_t* __restrict__ nzrow
 // about 1.3 rows per chunk on the Zipf workload) sums h by reduce-scatter, 17
 // shuffles, instead of the segmented scan's 5 (m + 1).
 template <typename T>
-__global__ void __launch_bounds__(256, 3) core_g_pass_kernel(DevModel<T> M, DevMode<T> csr, T* r, const T* __restrict__ U,
+__global__ void __launch_bounds__(256, 4) core_g_pass_kernel(DevModel<T> M, DevMode<T> csr, T* r, const T* __restrict__ U,
                                                           const T* __restrict__ A0c, GPassArgs a) {
   constexpr int kPer = kCoreMaxB / 32;
   __shared__ T sh[8][kCoreMaxM];
@@ -705,66 +735,76 @@ static vest_status vec_merge(const double* part, int nctas, int n, double* out, 
   return VEST_OK;
 }
 
-// Exact sequential updates of one block (Eq. 12 / Eq. 14) by one warp: lane
-// k % 32 holds the running sum_alpha r P(k) of element k, its value, mask and the
-// reciprocal of its denominator.  At step k the owning lane computes Delta_k alone
-// and broadcasts it; every lane then subtracts Delta_k M_kl from the elements l > k
-// it holds.
+// Exact sequential updates of one block (Eq. 12 / Eq. 14): thread l holds element l's
+// running sum g_l - sum_{k<l} M_kl Delta_k, its value, mask and the reciprocal of its
+// denominator.  At step k thread k computes the new value alone and posts Delta_k in shared
+// memory; after the step's barrier every thread l > k subtracts Delta_k M_kl.
+//
+// FP64 issues slowly on this part, so the block's elements are spread over four warps (one
+// per SM sub-partition) rather than held four to a lane in one warp: a step's FP64 work is
+// then one FMA on each sub-partition plus the owner's two, not four FMAs and the owner's work
+// on one.  The new value is one FMA (the terms that stay fixed during the solve are folded in
+// beforehand) and its rounding to the storage type is done on the bit pattern.  Thread counts
+// and the order of every operation are fixed, so the result does not depend on the device.
 template <typename T>
-__global__ void core_solve_kernel(DevModel<T> M, CoreBlock blk, int J0, int J1, int reg, double lambda,
-                                  const double* gram, const double* __restrict__ g, double* __restrict__ dout) {
-  constexpr int kPer = kCoreMaxB / 32;
+__global__ void __launch_bounds__(kCoreMaxB) core_solve_kernel(DevModel<T> M, CoreBlock blk, int J0, int J1, int reg,
+                                                               double lambda, const double* gram,
+                                                               const double* __restrict__ g, double* __restrict__ dout) {
   extern __shared__ double sgram[];
-  const int lane = threadIdx.x & 31;
+  __shared__ double s_dk[2];
+  __shared__ int s_upd[2];
+  const int l = threadIdx.x;
   const int b = blk.b;
-  for (int e = threadIdx.x; e < b * (b + 1) / 2; e += blockDim.x) sgram[e] = gram[e];
+  for (int e = l; e < b * (b + 1) / 2; e += blockDim.x) sgram[e] = gram[e];
   __syncthreads();
-  if (threadIdx.x >= 32) return;
   auto lin_of = [&](int k) {
     return (int64_t)(k % J0) + (int64_t)J0 * (blk.q0 + k / J0) + (int64_t)J0 * J1 * blk.s;
   };
-  double grad[kPer], gval[kPer], mkk[kPer], inv[kPer];
-  bool free_[kPer];
-#pragma unroll
-  for (int i = 0; i < kPer; ++i) {
-    const int l = lane + 32 * i;
-    const bool in = l < b;
-    grad[i] = in ? g[l] : 0.0;
-    gval[i] = in ? (double)M.G[lin_of(l)] : 0.0;
-    free_[i] = in && !M.Gmask[lin_of(l)];
-    mkk[i] = in ? sgram[sym_index(l, l, b)] : 1.0;
-    // Eq. 12: new = num / (lambda + M_kk); Eq. 14: new = -(g -/+ lambda) / (2 M_kk)
-    inv[i] = reg == VEST_REG_L1 ? 1.0 / (2.0 * mkk[i]) : 1.0 / (lambda + mkk[i]);
+  const bool l1 = reg == VEST_REG_L1;
+  const bool in = l < b;
+  // LF: new = grad * inv + cst, cst = old M_ll inv (Eq. 12: (grad + old M_ll) / (lambda + M_ll));
+  // L1: t = grad + cst, cst = old M_ll; new = (2t + lambda) / (2 M_ll) below -lambda / 2,
+  // (2t - lambda) / (2 M_ll) above lambda / 2, else 0 (Eq. 14 with g = -2t)
+  double grad = 0.0, gv = 0.0, iv = 0.0, cs = 0.0;
+  bool fr = false;
+  if (in) {
+    grad = g[l];
+    gv = (double)M.G[lin_of(l)];
+    fr = !M.Gmask[lin_of(l)];
+    const double mll = sgram[sym_index(l, l, b)];
+    iv = l1 ? 1.0 / (2.0 * mll) : 1.0 / (lambda + mll);
+    cs = l1 ? gv * mll : gv * mll * iv;
   }
+  const double half = 0.5 * lambda;
   for (int k = 0; k < b; ++k) {
-    double dk = 0.0;
-    if (lane == (k & 31)) {
-#pragma unroll
-      for (int i = 0; i < kPer; ++i) {
-        if (k / 32 == i && free_[i]) {
-          const double num = grad[i] + gval[i] * mkk[i];
-          double nv;
-          if (reg == VEST_REG_L1) {
-            const double gcv = -2.0 * num;
-            nv = gcv > lambda ? (lambda - gcv) * inv[i] : (gcv < -lambda ? -(lambda + gcv) * inv[i] : 0.0);
-          } else {
-            nv = num * inv[i];
-          }
-          const T st = (T)nv;
-          dk = (double)st - gval[i];
-          M.G[lin_of(k)] = st;
+    const bool later = in && l > k;
+    const double mkl = later ? sgram[sym_index(k, l, b)] : 0.0;
+    if (l == k) {
+      double dk = 0.0;
+      int upd = 0;
+      if (fr) {
+        double nv;
+        if (l1) {
+          const double t = grad + cs;
+          nv = t < -half ? fma(t, 2.0 * iv, lambda * iv) : (t > half ? fma(t, 2.0 * iv, -lambda * iv) : 0.0);
+        } else {
+          nv = fma(grad, iv, cs);
         }
+        const double nr = sizeof(T) == 4 ? round_to_single(nv) : nv;
+        M.G[lin_of(k)] = (T)nr;
+        const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(nr)),
+                                 o = static_cast<unsigned long long>(__double_as_longlong(gv));
+        upd = a != o && ((a | o) << 1) != 0ull;  // the value changed (either zero counts as equal)
+        if (upd) dk = nr - gv;
       }
       dout[k] = dk;
+      s_dk[k & 1] = dk;
+      s_upd[k & 1] = upd;
     }
-    dk = __shfl_sync(0xffffffffu, dk, k & 31);
-    if (dk != 0.0) {
-#pragma unroll
-      for (int i = 0; i < kPer; ++i) {
-        const int l = lane + 32 * i;
-        if (l > k && l < b) grad[i] -= dk * sgram[sym_index(k, l, b)];
-      }
-    }
+    // one barrier a step: the slots alternate, so step k + 1's post cannot overwrite the
+    // value a thread of step k has yet to read
+    __syncthreads();
+    if (s_upd[k & 1] && later) grad = fma(-s_dk[k & 1], mkl, grad);
   }
 }
 
@@ -836,6 +876,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
   // the coalesced loads of a chunk (row, its position in A0c, mode-1 index, mode-2 index
   // when N = 3, r) are issued one chunk ahead
   const bool n3 = M.N == 3;
+  const bool pair1 = rows_paired(M, 1, 0), pair2 = n3 && rows_paired(M, 2, a.s0);
   int nk = 0, ni1 = 0, ni2 = 0;
   T nrv = T(0);
   auto prefetch = [&](int64_t p) {
@@ -870,11 +911,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && J0B <= 16) ? 2 : 1)
           const T* a0 = A0c + (int64_t)k * J0;
           for (int j = 0; j < J0; ++j) se[j] = a0[j];
         }
-        const T* a1 = M.A[1] + (int64_t)i1 * J1;
-        for (int q = 0; q < J1; ++q) se[J0 + q] = a1[q];
+        copy_row<T>(M.A[1] + (int64_t)i1 * J1, J1, pair1, se + J0);
         if (n3) {
-          const T* a2 = M.A[2] + (int64_t)i2 * M.J[2] + a.s0;
-          for (int q = 0; q < Sg; ++q) se[J0 + J1 + q] = a2[q];
+          copy_row<T>(M.A[2] + (int64_t)i2 * M.J[2] + a.s0, Sg, pair2, se + J0 + J1);
         } else {
           suffix_weights<T>(M, csr.oidx, a.nnz, p, a.s0, Sg, se + J0 + J1, 1);
         }
@@ -1199,12 +1238,9 @@ static vest_status core_grams(const vest_index* ix, const DevModel<T>& M, const 
       core_gram_gemm_kernel<T><<<gg, 256, 0, s>>>(gm);
       VEST_LAUNCH("core_gram_gemm_kernel");
       const int b = c.J0 * mq, nm = b * (b + 1) / 2;
-      for (int si = 0; si < sg; ++si) {
-        const int64_t bi = (s0 + si) * c.nq0 + qc;
-        core_gram_merge_kernel<<<(unsigned)ceil_div(nm, 256), 256, 0, s>>>(bf.part, kGramKSplit, c.nX, ga.P, c.J0, mq,
-                                                                           nY, si, bf.gram + bi * c.nmmax);
-        VEST_LAUNCH("core_gram_merge_kernel");
-      }
+      core_gram_merge_kernel<<<dim3((unsigned)ceil_div(nm, 256), (unsigned)sg), 256, 0, s>>>(
+          bf.part, kGramKSplit, c.nX, ga.P, c.J0, mq, nY, s0, c.nq0, qc, c.nmmax, bf.gram);
+      VEST_LAUNCH("core_gram_merge_kernel");
     }
   }
   return VEST_OK;
@@ -1267,7 +1303,7 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
       const size_t ssm = (size_t)(blk.b * (blk.b + 1) / 2) * 8;
       auto sk = core_solve_kernel<T>;
       VEST_TRY(allow_smem(sk, ssm));
-      sk<<<1, 256, ssm, s>>>(M, blk, c.J0, c.J1, reg, lambda, bf.gram + iblk * c.nmmax, gvec, dbuf[iblk & 1]);
+      sk<<<1, kCoreMaxB, ssm, s>>>(M, blk, c.J0, c.J1, reg, lambda, bf.gram + iblk * c.nmmax, gvec, dbuf[iblk & 1]);
       VEST_LAUNCH("core_solve_kernel");
       a.prev = blk;
     }

@@ -71,6 +71,18 @@ struct vest_index {
 
 namespace vest {
 
+// x rounded to the nearest value with a 24-bit significand, ties to even (IEEE 754
+// round-to-nearest at single precision), by integer operations on the FP64 bit pattern:
+// the result equals (double)(float)x wherever that is a normal float.  Outside that range
+// (zero, float subnormals, overflow, inf, NaN) the conversion itself is used.
+__device__ __forceinline__ double round_to_single(double x) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int e = (int)((bits >> 52) & 0x7FF);
+  if (e < 1023 - 126 || e >= 1023 + 127) return (double)(float)x;
+  const unsigned long long lsb = (bits >> 29) & 1ull;
+  return __longlong_as_double(static_cast<long long>((bits + 0x0FFFFFFFull + lsb) & ~0x1FFFFFFFull));
+}
+
 // ------------------------------------------------------------------ device views
 template <typename T>
 struct DevModel {
