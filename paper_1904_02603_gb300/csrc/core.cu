@@ -723,10 +723,22 @@ __global__ void core_vec_merge_kernel(const double* __restrict__ part, int nctas
   }
 }
 
+// Groups of CTAs the first merge level forms from nctas per-CTA partials.
+static int merge_groups(int nctas) { return std::max(1, std::min(kMergeGroups, nctas / 8)); }
+
+// First level only: tmp[g][e] = sum over the CTAs of group g of part[c][e] (the block solve
+// adds the groups itself).
+static vest_status vec_merge_groups(const double* part, int nctas, int n, double* tmp, cudaStream_t s) {
+  const dim3 g1((unsigned)ceil_div(n, 32), (unsigned)merge_groups(nctas));
+  core_vec_merge1_kernel<<<g1, 256, 0, s>>>(part, nctas, n, tmp);
+  VEST_LAUNCH("core_vec_merge1_kernel");
+  return VEST_OK;
+}
+
 // sum over c < nctas of part[c][e] -> out[e], in two FP64 levels (groups of CTAs, then
 // the groups in order); tmp holds kMergeGroups x n doubles.
 static vest_status vec_merge(const double* part, int nctas, int n, double* out, double* tmp, cudaStream_t s) {
-  const int groups = std::max(1, std::min(kMergeGroups, nctas / 8));
+  const int groups = merge_groups(nctas);
   const dim3 g1((unsigned)ceil_div(n, 32), (unsigned)groups);
   core_vec_merge1_kernel<<<g1, 256, 0, s>>>(part, nctas, n, tmp);
   VEST_LAUNCH("core_vec_merge1_kernel");
@@ -746,10 +758,13 @@ static vest_status vec_merge(const double* part, int nctas, int n, double* out, 
 // on one.  The new value is one FMA (the terms that stay fixed during the solve are folded in
 // beforehand) and its rounding to the storage type is done on the bit pattern.  Thread counts
 // and the order of every operation are fixed, so the result does not depend on the device.
+// g arrives as ngroups partial vectors (the g pass's first merge level), g_l = the sum of
+// gpart[i][l] over i in a fixed order (four interleaved FP64 chains, then their sum).
 template <typename T>
 __global__ void __launch_bounds__(kCoreMaxB) core_solve_kernel(DevModel<T> M, CoreBlock blk, int J0, int J1, int reg,
                                                                double lambda, const double* gram,
-                                                               const double* __restrict__ g, double* __restrict__ dout) {
+                                                               const double* __restrict__ gpart, int ngroups,
+                                                               double* __restrict__ dout) {
   extern __shared__ double sgram[];
   __shared__ double s_dk[2];
   __shared__ int s_upd[2];
@@ -768,7 +783,16 @@ __global__ void __launch_bounds__(kCoreMaxB) core_solve_kernel(DevModel<T> M, Co
   double grad = 0.0, gv = 0.0, iv = 0.0, cs = 0.0;
   bool fr = false;
   if (in) {
-    grad = g[l];
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+    int i = 0;
+    for (; i + 3 < ngroups; i += 4) {
+      c0 += gpart[(size_t)i * b + l];
+      c1 += gpart[(size_t)(i + 1) * b + l];
+      c2 += gpart[(size_t)(i + 2) * b + l];
+      c3 += gpart[(size_t)(i + 3) * b + l];
+    }
+    for (; i < ngroups; ++i) c0 += gpart[(size_t)i * b + l];
+    grad = (c0 + c1) + (c2 + c3);
     gv = (double)M.G[lin_of(l)];
     fr = !M.Gmask[lin_of(l)];
     const double mll = sgram[sym_index(l, l, b)];
@@ -1255,7 +1279,6 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
   const CoreBufs bf = core_bufs(ix, mdl, scratch, plan);
   T* r0 = reinterpret_cast<T*>(scratch + plan.off_resid);
   double* out = bf.small + 9000 + 3 * kCoreMaxB;
-  double* gvec = bf.small + 9000 + 2 * kCoreMaxB;
   double* dbuf[2] = {bf.small + 9000, bf.small + 9000 + kCoreMaxB};
   VEST_TRY(loss_impl<T>(ix, mdl, reg, lambda, out, r0, nullptr, scratch, plan, s));
   VEST_TRY(core_grams<T>(ix, M, c, bf, s));
@@ -1271,6 +1294,8 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
   a.pair_u = reinterpret_cast<uintptr_t>(U) % (2 * sizeof(T)) == 0;
   const int nctas_g = kGPassCtas;
   const size_t gsm = (size_t)8 * 32 * c.J0 * sizeof(T);
+  double* gpart = bf.part + (size_t)kGPassCtas * kCoreMaxB;  // the g pass's merge groups, read by the solve
+  int ngroups = merge_groups(nctas_g);
   if (ix->nnz > 0) {
     core_a0c_kernel<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->mode[0].cap * c.J0, 256),
                                                                          num_sms() * 8)),
@@ -1296,14 +1321,15 @@ vest_status sweep_core_impl(const vest_index* ix, const vest_model* mdl, int reg
         }
         core_g_pass_kernel<T><<<nctas_g, 256, gsm, s>>>(M, csr, r0, U, A0c, a);
         VEST_LAUNCH("core_g_pass_kernel");
-        VEST_TRY(vec_merge(bf.part, nctas_g, blk.b, gvec, bf.part + (size_t)kGPassCtas * kCoreMaxB, s));
+        VEST_TRY(vec_merge_groups(bf.part, nctas_g, blk.b, gpart, s));
       } else {
-        VEST_CUDA(cudaMemsetAsync(gvec, 0, (size_t)blk.b * 8, s));
+        ngroups = 0;  // no entries: g = 0
       }
       const size_t ssm = (size_t)(blk.b * (blk.b + 1) / 2) * 8;
       auto sk = core_solve_kernel<T>;
       VEST_TRY(allow_smem(sk, ssm));
-      sk<<<1, kCoreMaxB, ssm, s>>>(M, blk, c.J0, c.J1, reg, lambda, bf.gram + iblk * c.nmmax, gvec, dbuf[iblk & 1]);
+      sk<<<1, kCoreMaxB, ssm, s>>>(M, blk, c.J0, c.J1, reg, lambda, bf.gram + iblk * c.nmmax, gpart, ngroups,
+                                   dbuf[iblk & 1]);
       VEST_LAUNCH("core_solve_kernel");
       a.prev = blk;
     }

@@ -30,6 +30,16 @@ struct SelectState {
   unsigned int hist[kSelBins];
 };
 
+// Every segment of one prune in one launch: blockIdx.y is the segment, each with its own
+// select state (the segments are independent, so 4 launches a pass become one).
+struct PruneSegs {
+  const double* delta[kMaxOrder + 1];
+  uint8_t* mask[kMaxOrder + 1];
+  void* val[kMaxOrder + 1];
+  int64_t size[kMaxOrder + 1];
+  int64_t* np[kMaxOrder + 1];
+};
+
 __device__ __forceinline__ uint64_t delta_key(double d) {
   if (d == 0.0) d = 0.0;  // -0 -> +0
   const uint64_t u = (uint64_t)__double_as_longlong(d);
@@ -54,13 +64,17 @@ __device__ __forceinline__ bool sel_match(uint64_t key, uint32_t idx, uint64_t p
 __host__ __device__ constexpr int sel_hi(int pass) { return 96 - kSelBits * pass; }
 __host__ __device__ constexpr int sel_lo(int pass) { return sel_hi(pass) - kSelBits > 0 ? sel_hi(pass) - kSelBits : 0; }
 
-// One histogram pass.  Pass 0 also counts the candidates and looks for NaN; its
-// last CTA turns pr into k.  The last CTA of every pass picks the digit of the
-// k-th pair and clears the histogram for the next pass.
-__global__ void __launch_bounds__(256) prune_select_kernel(const double* __restrict__ delta,
-                                                           const uint8_t* __restrict__ mask, int64_t size, int pass,
-                                                           double pr, int count_mode, SelectState* st,
-                                                           int64_t* __restrict__ n_pruned) {
+// One histogram pass of segment blockIdx.y.  Pass 0 also counts the candidates and looks for
+// NaN; its last CTA turns pr into k.  The last CTA of every pass picks the digit of the k-th
+// pair and clears the histogram for the next pass.
+__global__ void __launch_bounds__(256) prune_select_kernel(PruneSegs ps, int pass, double pr, int count_mode,
+                                                           SelectState* st_all) {
+  const int seg = blockIdx.y;
+  const double* __restrict__ delta = ps.delta[seg];
+  const uint8_t* __restrict__ mask = ps.mask[seg];
+  const int64_t size = ps.size[seg];
+  int64_t* __restrict__ n_pruned = ps.np[seg];
+  SelectState* st = st_all + seg;
   __shared__ unsigned sh[kSelBins];
   __shared__ unsigned long long s_cand;
   __shared__ int s_nan, s_last;
@@ -170,10 +184,17 @@ __global__ void __launch_bounds__(256) prune_select_kernel(const double* __restr
   for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) st->hist[b] = 0;
 }
 
-// Marks every candidate whose (key, index) is not above the selected pair: exactly k.
+// Marks every candidate whose (key, index) is not above the selected pair: exactly k
+// (segment blockIdx.y).
 template <typename T>
-__global__ void prune_mark_kernel(const double* __restrict__ delta, int64_t size, const SelectState* st,
-                                  uint8_t* __restrict__ mask, T* __restrict__ val, int64_t* __restrict__ n_pruned) {
+__global__ void prune_mark_kernel(PruneSegs ps, const SelectState* st_all) {
+  const int seg = blockIdx.y;
+  const double* __restrict__ delta = ps.delta[seg];
+  uint8_t* __restrict__ mask = ps.mask[seg];
+  T* __restrict__ val = static_cast<T*>(ps.val[seg]);
+  const int64_t size = ps.size[seg];
+  int64_t* __restrict__ n_pruned = ps.np[seg];
+  const SelectState* st = st_all + seg;
   if (st->done) return;
   const uint64_t pkey = st->pkey;
   const uint32_t pidx = st->pidx;
@@ -213,7 +234,32 @@ vest_status prune_impl(const vest_model* m, double* const* delta_factor, const d
   const DevModel<T> M = dev_model<T>(m);
   char* tmp = scratch + plan.off_prune_tmp;
   SelectState* st = reinterpret_cast<SelectState*>(tmp);
-  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(tmp + align_up(sizeof(SelectState)));
+  unsigned long long* cnt =
+      reinterpret_cast<unsigned long long*>(tmp + align_up((size_t)(kMaxOrder + 1) * sizeof(SelectState)));
+  if (!threshold_mode) {
+    PruneSegs ps{};
+    int grid = 1;
+    for (int seg = 0; seg <= M.N; ++seg) {
+      const bool core = seg == M.N;
+      const int64_t size = core ? M.gsize : M.I[seg] * M.J[seg];
+      if (size > 0xFFFFFFFFll) return fail(VEST_ERR_UNSUPPORTED, "prune: a segment holds 2^32 elements or more");
+      ps.delta[seg] = core ? delta_core : delta_factor[seg];
+      ps.mask[seg] = core ? M.Gmask : M.mask[seg];
+      ps.val[seg] = core ? M.G : M.A[seg];
+      ps.size[seg] = size;
+      ps.np[seg] = n_pruned ? n_pruned + seg : nullptr;
+      grid = std::max(grid, std::max(1, std::min<int>((int)ceil_div(size, 256), num_sms() * 4)));
+    }
+    const dim3 g((unsigned)grid, (unsigned)(M.N + 1));
+    VEST_CUDA(cudaMemsetAsync(st, 0, (size_t)(M.N + 1) * sizeof(SelectState), s));
+    for (int pass = 0; pass < kSelPasses; ++pass) {
+      prune_select_kernel<<<g, 256, 0, s>>>(ps, pass, pr, count_mode, st);
+      VEST_LAUNCH("prune_select");
+    }
+    prune_mark_kernel<T><<<g, 256, 0, s>>>(ps, st);
+    VEST_LAUNCH("prune_mark");
+    return VEST_OK;
+  }
   for (int seg = 0; seg <= M.N; ++seg) {
     const bool core = seg == M.N;
     const int64_t size = core ? M.gsize : M.I[seg] * M.J[seg];
@@ -223,23 +269,13 @@ vest_status prune_impl(const vest_model* m, double* const* delta_factor, const d
     int64_t* np = n_pruned ? n_pruned + seg : nullptr;
     const int grid = std::max(1, std::min<int>((int)ceil_div(size, 256), num_sms() * 4));
     if (size > 0xFFFFFFFFll) return fail(VEST_ERR_UNSUPPORTED, "prune: a segment holds 2^32 elements or more");
-    if (threshold_mode) {
-      VEST_CUDA(cudaMemsetAsync(cnt, 0, sizeof(*cnt), s));
-      prune_threshold_kernel<T><<<grid, 256, 0, s>>>(dl, size, tau, mask, val, cnt);
-      VEST_LAUNCH("prune_threshold");
-      if (np) {
-        copy_count_kernel<<<1, 1, 0, s>>>(cnt, np);
-        VEST_LAUNCH("copy_count");
-      }
-      continue;
+    VEST_CUDA(cudaMemsetAsync(cnt, 0, sizeof(*cnt), s));
+    prune_threshold_kernel<T><<<grid, 256, 0, s>>>(dl, size, tau, mask, val, cnt);
+    VEST_LAUNCH("prune_threshold");
+    if (np) {
+      copy_count_kernel<<<1, 1, 0, s>>>(cnt, np);
+      VEST_LAUNCH("copy_count");
     }
-    VEST_CUDA(cudaMemsetAsync(st, 0, sizeof(SelectState), s));
-    for (int pass = 0; pass < kSelPasses; ++pass) {
-      prune_select_kernel<<<grid, 256, 0, s>>>(dl, mask, size, pass, pr, count_mode, st, np);
-      VEST_LAUNCH("prune_select");
-    }
-    prune_mark_kernel<T><<<grid, 256, 0, s>>>(dl, size, st, mask, val, np);
-    VEST_LAUNCH("prune_mark");
   }
   return VEST_OK;
 }
@@ -270,7 +306,7 @@ size_t prune_scratch_bytes(int64_t maxseg, size_t* keys_bytes, size_t* vals_byte
   (void)maxseg;
   *keys_bytes = 0;
   *vals_bytes = 0;
-  *tmp_bytes = align_up(sizeof(SelectState)) + 256;
+  *tmp_bytes = align_up((size_t)(kMaxOrder + 1) * sizeof(SelectState)) + 256;
   return *keys_bytes + *vals_bytes + *tmp_bytes;
 }
 
