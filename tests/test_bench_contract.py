@@ -33,3 +33,29 @@ def test_reference_arm_on_other_ranks_and_other_workloads():
                 env={"RANK": "1", "WORLD_SIZE": "2"}) == []
     lines = _run("--impl", "reference", "--workload", "batch_256_jobs", "--steps", "1", "--warmup", "1")
     assert len(lines) == 1 and lines[0]["impl"] == "reference" and "unavailable" in lines[0]
+
+
+def _copy_tree_for_traffic(tmp_path):
+    """The files profiled_traffic reads: the committed summaries and the kernel sources."""
+    import shutil
+    root = tmp_path / "repo"
+    shutil.copytree(os.path.join(ROOT, "profiles"), root / "profiles")
+    shutil.copytree(os.path.join(ROOT, "paper_1904_02603_gb300", "csrc"), root / "paper_1904_02603_gb300" / "csrc")
+    return root
+
+
+def test_roofline_traffic_comes_from_the_summary_while_its_sources_match(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    root = _copy_tree_for_traffic(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    text = (root / "profiles" / "sweep_task_tc_kernel_zipf_1e5x3_1e7.md").read_text()
+    want = float(next(l for l in text.splitlines() if l.startswith("dram_bytes_per_launch:")).split(":", 1)[1])
+    traffic, source = bench.profiled_traffic("zipf_1e5x3_1e7", True)
+    assert traffic == want and "sweep_task_tc_kernel_zipf_1e5x3_1e7.md" in source
+    # a workload without a summary, and a kernel source changed after the capture: no traffic
+    assert bench.profiled_traffic("uniform_1e4x4_5e7", True)[0] is None
+    src = root / "paper_1904_02603_gb300" / "csrc" / "tc_delta.cuh"
+    src.write_text(src.read_text() + "\n// edited after the capture\n")
+    traffic, why = bench.profiled_traffic("zipf_1e5x3_1e7", True)
+    assert traffic is None and "changed" in why
